@@ -1,0 +1,153 @@
+/*
+ * polarscl.h -- C ABI of the GB300 polar list decoder (libpolarscl.so).
+ *
+ * Batched successive-cancellation list decoding of polar codes with CRC aid,
+ * tree pruning, fixed-point LLRs and adaptive list schedules, after Leonardon
+ * et al., "Fast and Flexible Software Polar List Decoders" (SCL in Sec. II-B
+ * and Algorithm 1; genericity and flexibility in Sec. III; CRC, sorting and
+ * partial sums in Sec. IV).
+ *
+ * Conventions shared by every call:
+ *  - A code has length N = 2^n (8 <= N <= 2048), |A| = K information
+ *    positions that INCLUDE the c CRC bits (K_info = K - c data bits).  Data
+ *    bits then CRC bits fill A in increasing position order.  The CRC is the
+ *    MSB-first remainder of the data bits times x^c modulo x^c + crc_poly
+ *    (initial value 0, no reflection, no final XOR).
+ *  - Encoding (Sec. II-A): x = u F^{(x)n}, F = [[1,0],[1,1]]; systematic codes
+ *    re-encode after zeroing the frozen part so that x_A = u_A.
+ *  - LLRs are ln P(x=0)/P(x=1); BPSK maps 0 -> +1.  A frame's LLR row holds
+ *    the N - P transmitted positions in increasing position order; punctured
+ *    positions get LLR 0 inside the decoder.
+ *  - Bit vectors passed as bytes are packed MSB first: bit i is bit 7 - (i&7)
+ *    of byte i >> 3.
+ *  - Every device buffer belongs to the caller.  Calls are asynchronous on the
+ *    given CUDA stream (a cudaStream_t passed as void*, NULL = legacy default
+ *    stream) and return after enqueueing.  Argument errors are reported
+ *    before anything is enqueued.
+ *  - Return value: PSCL_OK (0) or a negative PSCL_E* code; pscl_last_error()
+ *    returns a message for the calling thread's last failure.
+ */
+#ifndef POLARSCL_H
+#define POLARSCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSCL_OK 0
+#define PSCL_EINVAL (-1)       /* an argument is out of range */
+#define PSCL_ENOMEM (-2)       /* a device or host allocation failed */
+#define PSCL_EUNSUPPORTED (-3) /* valid, but not supported by the kernels */
+#define PSCL_ECUDA (-4)        /* a CUDA call failed (message has the details) */
+#define PSCL_ETIMEDOUT (-5)    /* a bounded wait ran out */
+#define PSCL_EAGAIN (-6)       /* a queue is full; retry later */
+
+typedef struct pscl_code_s *pscl_code;
+
+/* Decoding algorithms (Sec. II-B): SC is the list of one; CASCL keeps L paths
+ * and picks the best-metric candidate that passes the CRC (Sec. IV-A);
+ * FASCL decodes with L = 1, 2, 4, ..., L and stops at the first CRC pass;
+ * PASCL decodes with L = 1 and then directly with L.                        */
+typedef enum { PSCL_SC = 0, PSCL_CASCL = 1, PSCL_PASCL = 2, PSCL_FASCL = 3 } pscl_algo;
+
+/* LLR and metric representation (Sec. III-B-3).  Input LLRs are always float;
+ * the fixed-point paths quantise q = clamp(rint_half_even(llr * 2^f), -Q, Q)
+ * with (f, Q) = (5, 32767) for I16 and (2, 127) for I8, and saturate every
+ * addition to [-Q, Q]; their metrics are normalised by subtracting the
+ * smallest active metric after every step.                                 */
+typedef enum { PSCL_F32 = 0, PSCL_I16 = 1, PSCL_I8 = 2 } pscl_quant;
+
+#define PSCL_PRUNE_R0 1u
+#define PSCL_PRUNE_R1 2u
+#define PSCL_PRUNE_REP 4u
+#define PSCL_PRUNE_SPC 8u
+
+/* Tree pruning (Sec. II-B, Sec. III-B-2): the top-most node whose leaves are
+ * all frozen (R0), all information (R1), all frozen but the last (REP) or
+ * only the first frozen (SPC) is decoded as a whole if its type is enabled
+ * in `mask` and its size is within the limit; precedence R0 > R1 > REP > SPC.
+ * rep_max: 0 = no limit (REP2+), 8 = REP8-.  spc_max: 4 = SPC4 (size 4
+ * only), 0 = no limit (SPC4+).  r1_max: 0 = no limit.  r1_t / spc_t: how many
+ * least-reliable positions the R1 / SPC candidates flip (r1_t = 2 is the
+ * paper's Chase-2, Sec. IV-B); the kernels accept 1 <= r1_t <= 4 and
+ * 1 <= spc_t <= 5.  mask = 0 decodes the full tree leaf by leaf.            */
+typedef struct {
+    uint32_t mask;
+    int rep_max;
+    int spc_max;
+    int r1_t;
+    int spc_t;
+    int r1_max;
+} pscl_pruning;
+
+/* Create a code descriptor and upload it to the current CUDA device.
+ * frozen: host, N bytes, nonzero = frozen; exactly N - K of them.
+ * crc_len: 0, 8, 16 or 32; crc_poly: generator without its top bit
+ * (e.g. 0x07, 0x1021, 0x04C11DB7); crc_len <= K.
+ * puncture: host, N bytes, nonzero = not transmitted, or NULL.
+ * systematic: 1 for systematic encoding (the paper's), 0 for x = u F.
+ * On success *out owns device memory until pscl_destroy_code.
+ * Errors: PSCL_EINVAL (bad N, K, counts, CRC), PSCL_ENOMEM, PSCL_ECUDA.   */
+int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len, uint32_t crc_poly,
+                     const uint8_t *puncture, int systematic, pscl_code *out);
+
+/* Free a descriptor.  The caller must make sure no queued work still uses
+ * it (e.g. synchronise the streams it was used on).                        */
+int pscl_destroy_code(pscl_code code);
+
+/* Query code parameters (any pointer may be NULL).                          */
+int pscl_code_info(pscl_code code, int *N, int *K, int *K_info, int *n_punctured);
+
+/* Build (once per pruning setting) the node schedule the kernels walk for
+ * this code, and cache it with the code.  pscl_decode calls this itself;
+ * call it first when decodes will be captured in a CUDA graph, because the
+ * first build makes a synchronous upload.                                   */
+int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
+
+/* Decode n_frames frames (Algorithm 1 with the selected algorithm).
+ * llr: device, n_frames x (N - P) float32, row-major.
+ * L: list size (maximum list size for FASCL/PASCL), one of 1, 2, 4, 8, 16, 32.
+ * pruning: NULL = no pruning.
+ * info_out: device, n_frames x ceil(K_info / 8) bytes, packed MSB first.
+ * status_out: device, int32 per frame: bit 0 = the output passed the CRC
+ *   (always 1 when crc_len = 0), bits 8..15 = list size of the stage that
+ *   produced it, bits 16..23 = its path slot.
+ * pm_out: device or NULL; n_frames x L float32 path metrics of the final
+ *   stage in slot order (fixed point converted exactly), +inf for unused
+ *   slots.
+ * The library keeps a per-device scratch workspace that it grows on demand
+ * (a synchronous cudaMalloc): call once outside stream capture before
+ * capturing, or use pscl_decode_ws.                                          */
+int pscl_decode(pscl_code code, const float *llr, int n_frames, int L, pscl_algo algo,
+                const pscl_pruning *pruning, pscl_quant quant, uint8_t *info_out,
+                int32_t *status_out, float *pm_out, void *stream);
+
+/* Bytes of device workspace pscl_decode_ws needs for this call shape.       */
+int pscl_workspace_size(pscl_code code, int n_frames, int L, pscl_algo algo,
+                        const pscl_pruning *pruning, pscl_quant quant, size_t *bytes);
+
+/* pscl_decode with a caller-provided workspace (device, 256-byte aligned, at
+ * least pscl_workspace_size bytes); allocates nothing.                      */
+int pscl_decode_ws(pscl_code code, const float *llr, int n_frames, int L, pscl_algo algo,
+                   const pscl_pruning *pruning, pscl_quant quant, uint8_t *info_out,
+                   int32_t *status_out, float *pm_out, void *workspace, size_t workspace_bytes,
+                   void *stream);
+
+/* Encode n_frames frames (Sec. II-A): info: device, n_frames x
+ * ceil(K_info/8) bytes packed MSB first; x_out: device, n_frames x N bytes,
+ * one codeword bit (0/1) per byte, punctured positions included.           */
+int pscl_encode(pscl_code code, const uint8_t *info, int n_frames, uint8_t *x_out, void *stream);
+
+/* Message for the calling thread's most recent error ("" if none).         */
+const char *pscl_last_error(void);
+
+/* Library version string.                                                   */
+const char *pscl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,636 @@
+// api.cu -- host side of libpolarscl: the C ABI declared in include/polarscl.h.
+//
+// Code descriptors (Sec. III-A genericity: N, frozen set, CRC and puncturing
+// are run-time data), the node schedule built per pruning setting (Sec. II-B,
+// III-B-2), the per-warp memory layout, the workspace and the launches.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/polarscl.h"
+#include "internal.h"
+
+using namespace pscl;
+
+// ---------------------------------------------------------------------------
+// errors
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? PSCL_ENOMEM : PSCL_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                       \
+    } while (0)
+
+extern "C" const char *pscl_last_error(void) { return g_err.c_str(); }
+extern "C" const char *pscl_version(void) { return "polarscl 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// device properties
+struct DevProps {
+    int sms = 0;
+    int smem_optin = 0;
+    int smem_per_sm = 0;
+};
+static std::mutex g_mu;
+static std::map<int, DevProps> g_props;
+
+static int get_props(DevProps *out)
+{
+    int dev;
+    CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_props.find(dev);
+    if (it == g_props.end()) {
+        DevProps p;
+        CU(cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev));
+        CU(cudaDeviceGetAttribute(&p.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        CU(cudaDeviceGetAttribute(&p.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        it = g_props.emplace(dev, p).first;
+    }
+    *out = it->second;
+    return PSCL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// code descriptor
+struct Program {
+    uint32_t *d_ops = nullptr;
+    int n_ops = 0;
+    int max_depth = 0;
+    int root_special = 0;
+};
+
+struct pscl_code_s {
+    int dev = -1;
+    int N = 0, n = 0, K = 0, kinfo = 0, crc_len = 0, P = 0, systematic = 1;
+    uint32_t crc_poly = 0;
+    std::vector<uint8_t> frozen, punct;
+    DevCode dc;
+    void *d_blob = nullptr;
+    std::mutex mu;
+    std::map<std::vector<int>, Program> programs;
+};
+
+static uint32_t crc_poly32(int c, uint32_t poly)
+{
+    if (c == 0) return 0;
+    uint32_t mask = c == 32 ? 0xFFFFFFFFu : ((1u << c) - 1u);
+    return (poly & mask) << (32 - c);
+}
+
+extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len, uint32_t crc_poly,
+                                const uint8_t *puncture, int systematic, pscl_code *out)
+{
+    if (!out) return fail(PSCL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < 8 || N > 2048 || (N & (N - 1))) return fail(PSCL_EINVAL, "N=%d: must be a power of two in [8, 2048]", N);
+    if (!frozen) return fail(PSCL_EINVAL, "frozen is NULL");
+    if (crc_len != 0 && crc_len != 8 && crc_len != 16 && crc_len != 32)
+        return fail(PSCL_EINVAL, "crc_len=%d: must be 0, 8, 16 or 32", crc_len);
+    int nf = 0;
+    for (int i = 0; i < N; i++) nf += frozen[i] ? 1 : 0;
+    if (N - nf != K || K < 1) return fail(PSCL_EINVAL, "K=%d but the frozen set leaves %d positions", K, N - nf);
+    if (crc_len > K) return fail(PSCL_EINVAL, "crc_len=%d exceeds K=%d", crc_len, K);
+    int P = 0;
+    if (puncture)
+        for (int i = 0; i < N; i++) P += puncture[i] ? 1 : 0;
+    if (P >= N) return fail(PSCL_EINVAL, "every position is punctured");
+
+    pscl_code_s *c = new pscl_code_s();
+    c->N = N;
+    c->n = 0;
+    while ((1 << c->n) < N) c->n++;
+    c->K = K;
+    c->kinfo = K - crc_len;
+    c->crc_len = crc_len;
+    c->crc_poly = crc_poly;
+    c->P = P;
+    c->systematic = systematic ? 1 : 0;
+    c->frozen.assign(frozen, frozen + N);
+    for (auto &v : c->frozen) v = v ? 1 : 0;
+    c->punct.assign(N, 0);
+    if (puncture)
+        for (int i = 0; i < N; i++) c->punct[i] = puncture[i] ? 1 : 0;
+
+    // host images of the device arrays
+    std::vector<int32_t> in_index(N);
+    for (int i = 0, k = 0; i < N; i++) in_index[i] = c->punct[i] ? -1 : k++;
+    std::vector<uint16_t> A;
+    for (int i = 0; i < N; i++)
+        if (!c->frozen[i]) A.push_back((uint16_t)i);
+    const int NW = N >= 32 ? N / 32 : 1;
+    std::vector<uint32_t> amask(NW, 0);
+    for (int i = 0; i < N; i++)
+        if (!c->frozen[i]) amask[i >> 5] |= 1u << (i & 31);
+    std::vector<uint32_t> lut(256, 0);
+    const uint32_t p32 = crc_poly32(crc_len, crc_poly);
+    for (uint32_t b = 0; b < 256; b++) {
+        uint32_t r = b << 24;
+        for (int k = 0; k < 8; k++) r = (r & 0x80000000u) ? ((r << 1) ^ p32) : (r << 1);
+        lut[b] = r;
+    }
+    size_t off_in = 0, off_A = off_in + 4 * (size_t)N, off_am = off_A + ((2 * (size_t)K + 15) & ~(size_t)15),
+           off_lut = off_am + ((4 * (size_t)NW + 15) & ~(size_t)15), total = off_lut + 1024;
+    std::vector<uint8_t> blob(total, 0);
+    memcpy(blob.data() + off_in, in_index.data(), 4 * (size_t)N);
+    memcpy(blob.data() + off_A, A.data(), 2 * (size_t)K);
+    memcpy(blob.data() + off_am, amask.data(), 4 * (size_t)NW);
+    memcpy(blob.data() + off_lut, lut.data(), 1024);
+    cudaError_t e = cudaGetDevice(&c->dev);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_blob, total);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (c->d_blob) cudaFree(c->d_blob);
+        delete c;
+        return fail(e == cudaErrorMemoryAllocation ? PSCL_ENOMEM : PSCL_ECUDA, "create_code: %s",
+                    cudaGetErrorString(e));
+    }
+    char *base = (char *)c->d_blob;
+    DevCode &dc = c->dc;
+    dc.N = N;
+    dc.n = c->n;
+    dc.K = K;
+    dc.kinfo = c->kinfo;
+    dc.crc_len = crc_len;
+    dc.systematic = c->systematic;
+    dc.P = P;
+    dc.poly32 = p32;
+    dc.in_index = (const int32_t *)(base + off_in);
+    dc.A = (const uint16_t *)(base + off_A);
+    dc.amask = (const uint32_t *)(base + off_am);
+    dc.crc_lut = (const uint32_t *)(base + off_lut);
+    *out = c;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_destroy_code(pscl_code c)
+{
+    if (!c) return fail(PSCL_EINVAL, "code is NULL");
+    for (auto &kv : c->programs) cudaFree(kv.second.d_ops);
+    cudaFree(c->d_blob);
+    delete c;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_code_info(pscl_code c, int *N, int *K, int *K_info, int *n_punctured)
+{
+    if (!c) return fail(PSCL_EINVAL, "code is NULL");
+    if (N) *N = c->N;
+    if (K) *K = c->K;
+    if (K_info) *K_info = c->kinfo;
+    if (n_punctured) *n_punctured = c->P;
+    return PSCL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// node schedule (Sec. II-B tree pruning): pre-order traversal of Algorithm 1;
+// a node whose leaves are all frozen (R0), all information (R1), all frozen
+// but the last (REP) or only the first frozen (SPC) becomes one step when its
+// type is enabled and within its size limit, the top-most such node winning.
+static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
+{
+    int nf = 0;
+    for (int i = o; i < o + S; i++) nf += c->frozen[i];
+    if (S == 1) return nf ? NT_R0 : NT_R1;
+    if (!pr) return 0;
+    if (nf == S && (pr->mask & PSCL_PRUNE_R0)) return NT_R0;
+    if (nf == 0 && (pr->mask & PSCL_PRUNE_R1) && (pr->r1_max == 0 || S <= pr->r1_max)) return NT_R1;
+    if (nf == S - 1 && !c->frozen[o + S - 1] && (pr->mask & PSCL_PRUNE_REP) && (pr->rep_max == 0 || S <= pr->rep_max))
+        return NT_REP;
+    if (nf == 1 && c->frozen[o] && S >= 4 && (pr->mask & PSCL_PRUNE_SPC) && (pr->spc_max == 0 || S <= pr->spc_max))
+        return NT_SPC;
+    return 0;
+}
+
+static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int o, int S, int side,
+                       std::vector<uint32_t> &ops, int &max_depth)
+{
+    int type = classify(c, pr, o, S);
+    if (type) {
+        int t = 0;
+        if (type == NT_R1) {
+            int r1t = pr ? pr->r1_t : 1;
+            t = S == 1 ? 1 : (r1t < S ? r1t : S);
+            if (t < 1 || t > 4) return fail(PSCL_EUNSUPPORTED, "R1 flip depth %d (node size %d) outside 1..4", t, S);
+        } else if (type == NT_SPC) {
+            t = pr->spc_t < S ? pr->spc_t : S;
+            if (t < 1 || t > 5) return fail(PSCL_EUNSUPPORTED, "SPC flip depth %d (node size %d) outside 1..5", t, S);
+        }
+        ops.push_back(op_make(OP_NODE, (uint32_t)d, (uint32_t)type, (uint32_t)side, (uint32_t)t));
+        if (d > max_depth) max_depth = d;
+        return PSCL_OK;
+    }
+    ops.push_back(op_make(OP_F, (uint32_t)d, 0, 0, 0));
+    int rc = gen_program(c, pr, d + 1, o, S / 2, 0, ops, max_depth);
+    if (rc) return rc;
+    ops.push_back(op_make(OP_G, (uint32_t)d, 0, 0, 0));
+    rc = gen_program(c, pr, d + 1, o + S / 2, S / 2, 1, ops, max_depth);
+    if (rc) return rc;
+    if (d > 0) ops.push_back(op_make(OP_COMB, (uint32_t)(d + 1), 0, (uint32_t)side, 0));
+    return PSCL_OK;
+}
+
+static std::vector<int> prune_key(const pscl_pruning *pr)
+{
+    if (!pr || pr->mask == 0) return {0};
+    return {(int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
+}
+
+static int check_pruning(const pscl_pruning *pr)
+{
+    if (!pr || pr->mask == 0) return PSCL_OK;
+    if (pr->mask & ~15u) return fail(PSCL_EINVAL, "pruning mask 0x%x has unknown bits", pr->mask);
+    if (pr->rep_max < 0 || pr->spc_max < 0 || pr->r1_max < 0)
+        return fail(PSCL_EINVAL, "negative pruning size limit");
+    if ((pr->mask & PSCL_PRUNE_R1) && (pr->r1_t < 1 || pr->r1_t > 4))
+        return fail(PSCL_EUNSUPPORTED, "r1_t=%d: the kernels support 1..4", pr->r1_t);
+    if ((pr->mask & PSCL_PRUNE_SPC) && (pr->spc_t < 1 || pr->spc_t > 5))
+        return fail(PSCL_EUNSUPPORTED, "spc_t=%d: the kernels support 1..5", pr->spc_t);
+    return PSCL_OK;
+}
+
+static int get_program(pscl_code c, const pscl_pruning *pr, Program *out)
+{
+    int rc = check_pruning(pr);
+    if (rc) return rc;
+    const pscl_pruning *eff = (pr && pr->mask) ? pr : nullptr;
+    std::vector<int> key = prune_key(pr);
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->programs.find(key);
+    if (it != c->programs.end()) {
+        *out = it->second;
+        return PSCL_OK;
+    }
+    std::vector<uint32_t> ops;
+    int max_depth = 0;
+    rc = gen_program(c, eff, 0, 0, c->N, 1, ops, max_depth);
+    if (rc) return rc;
+    Program p;
+    p.n_ops = (int)ops.size();
+    p.max_depth = max_depth;
+    p.root_special = (op_code(ops[0]) == OP_NODE) ? 1 : 0;
+    CU(cudaMalloc(&p.d_ops, ops.size() * sizeof(uint32_t)));
+    cudaError_t e = cudaMemcpy(p.d_ops, ops.data(), ops.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p.d_ops);
+        return fail(PSCL_ECUDA, "program upload: %s", cudaGetErrorString(e));
+    }
+    c->programs[key] = p;
+    *out = p;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
+{
+    if (!c) return fail(PSCL_EINVAL, "code is NULL");
+    Program p;
+    return get_program(c, pr, &p);
+}
+
+// ---------------------------------------------------------------------------
+// per-warp memory layout: every buffer goes to shared memory while the budget
+// lasts, deepest (smallest, most often touched) layers first; the rest lives
+// in the warp's global scratch slice.
+static void make_layout(const pscl_code_s *c, const Program &pg, int L, int quant, size_t smem_budget, Layout *lay)
+{
+    memset(lay, 0, sizeof(*lay));
+    const int EPW = quant == PSCL_F32 ? 1 : (quant == PSCL_I16 ? 2 : 4);
+    const int fpw = 32 / L;
+    uint32_t so = 0, go = 0;
+    auto align16 = [](uint32_t v) { return (v + 15u) & ~15u; };
+    // selection scatter (64 words) + frame ids (32 words)
+    lay->src_off = 0;
+    so = align16(96 * 4);
+    const int maxd = pg.max_depth;
+    for (int d = maxd; d >= 0; d--) {
+        const int S = c->N >> d;
+        const uint32_t rows = (uint32_t)((S + EPW - 1) / EPW);
+        const uint32_t words = rows * (uint32_t)(d == 0 ? fpw : 32);
+        const uint32_t bwords = (uint32_t)(S >= 32 ? S / 32 : 1) * 32u;
+        // LLR layer d
+        lay->llr_words[d] = words;
+        if (so + words * 4 <= smem_budget) {
+            lay->llr_off[d] = so;
+            lay->llr_smem |= 1u << d;
+            so = align16(so + words * 4);
+        } else {
+            lay->llr_off[d] = go;
+            go = align16(go + words * 4);
+        }
+        // partial-sum buffers: BL_d, BR_d for d >= 1; BR_0 when the root is a node
+        lay->b_words[d] = bwords;
+        const bool need_bl = d >= 1, need_br = d >= 1 || pg.root_special;
+        if (need_bl) {
+            if (so + bwords * 4 <= smem_budget) {
+                lay->bl_off[d] = so;
+                lay->bl_smem |= 1u << d;
+                so = align16(so + bwords * 4);
+            } else {
+                lay->bl_off[d] = go;
+                go = align16(go + bwords * 4);
+            }
+        }
+        if (need_br) {
+            if (so + bwords * 4 <= smem_budget) {
+                lay->br_off[d] = so;
+                lay->br_smem |= 1u << d;
+                so = align16(so + bwords * 4);
+            } else {
+                lay->br_off[d] = go;
+                go = align16(go + bwords * 4);
+            }
+        }
+    }
+    if (!c->systematic) {
+        lay->ns_words = (uint32_t)(c->N >= 32 ? c->N / 32 : 1) * 32u;
+        lay->ns_off = go;
+        go = align16(go + lay->ns_words * 4);
+    }
+    lay->smem_per_warp = so;
+    lay->gmem_per_warp = (go + 255u) & ~255u;
+}
+
+// ---------------------------------------------------------------------------
+// launch plan for one decode call
+struct Plan {
+    Program pg;
+    Layout lay;
+    int warps_per_block = 4;
+    int grid = 0;
+    int total_warps = 0;
+    size_t smem_block = 0;
+    size_t gmem_scratch = 0;   // per-warp slices
+    size_t list_bytes = 0;     // adaptive frame lists + counters
+    size_t total_ws = 0;
+    int n_stages = 0;
+    int stages[8];
+};
+
+static const int kWarpsPerBlock = 4;
+// target resident warps per SM; each warp's shared slice is sized to fit
+static int g_target_warps_per_sm = 8;
+
+static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const pscl_pruning *pr, pscl_quant quant,
+                     Plan *pl)
+{
+    if (!c) return fail(PSCL_EINVAL, "code is NULL");
+    if (n_frames < 0) return fail(PSCL_EINVAL, "n_frames=%d", n_frames);
+    if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32)
+        return fail(PSCL_EINVAL, "L=%d: must be 1, 2, 4, 8, 16 or 32", L);
+    if (algo < PSCL_SC || algo > PSCL_FASCL) return fail(PSCL_EINVAL, "unknown algorithm %d", (int)algo);
+    if (quant < PSCL_F32 || quant > PSCL_I8) return fail(PSCL_EINVAL, "unknown quantisation %d", (int)quant);
+    int dev;
+    CU(cudaGetDevice(&dev));
+    if (dev != c->dev) return fail(PSCL_EINVAL, "code was created on device %d, current device is %d", c->dev, dev);
+    int rc = get_program(c, pr, &pl->pg);
+    if (rc) return rc;
+    DevProps dp;
+    rc = get_props(&dp);
+    if (rc) return rc;
+    // stages of the algorithm
+    pl->n_stages = 0;
+    if (algo == PSCL_SC) pl->stages[pl->n_stages++] = 1;
+    else if (algo == PSCL_CASCL) pl->stages[pl->n_stages++] = L;
+    else if (algo == PSCL_FASCL) {
+        for (int l = 1; l < L; l *= 2) pl->stages[pl->n_stages++] = l;
+        pl->stages[pl->n_stages++] = L;
+    } else {
+        pl->stages[pl->n_stages++] = 1;
+        if (L > 1) pl->stages[pl->n_stages++] = L;
+    }
+    // layout: the largest stage list size determines frames per warp, but
+    // every stage uses the same per-warp slices (the layout of the smallest
+    // list size needs the most layer-0 room, the largest the most paths:
+    // both only depend on N, EPW and 32/L for layer 0)
+    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
+    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
+    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    // each stage recomputes its own layout at launch; the plan keeps maxima
+    uint32_t max_smem = 0, max_gmem = 0;
+    for (int s = 0; s < pl->n_stages; s++) {
+        Layout l;
+        make_layout(c, pl->pg, pl->stages[s], (int)quant, budget, &l);
+        if (l.smem_per_warp > max_smem) max_smem = l.smem_per_warp;
+        if (l.gmem_per_warp > max_gmem) max_gmem = l.gmem_per_warp;
+    }
+    pl->smem_block = (size_t)max_smem * kWarpsPerBlock;
+    int bps = 0;
+    cudaError_t e = scl_func_attrs((int)quant, pl->smem_block, 32 * kWarpsPerBlock, &bps);
+    if (e != cudaSuccess) return fail(PSCL_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+    if (bps < 1) return fail(PSCL_EUNSUPPORTED, "no block fits (shared memory %zu bytes)", pl->smem_block);
+    const int max_warps = dp.sms * bps * kWarpsPerBlock;
+    const int fpw_min = 32 / pl->stages[pl->n_stages - 1];
+    long long tasks = ((long long)n_frames + fpw_min - 1) / fpw_min;
+    long long want = tasks < 1 ? 1 : tasks;
+    // the first stage may have more frames per warp; size the grid for the
+    // stage with the most tasks
+    long long tasks0 = ((long long)n_frames + (32 / pl->stages[0]) - 1) / (32 / pl->stages[0]);
+    if (tasks0 > want) want = tasks0;
+    int tw = (int)(want < max_warps ? want : max_warps);
+    pl->grid = (tw + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    pl->total_warps = pl->grid * kWarpsPerBlock;
+    pl->gmem_scratch = (size_t)max_gmem * (size_t)pl->total_warps;
+    pl->list_bytes = pl->n_stages > 1 ? (2 * (size_t)n_frames * 4 + 256 + 255) & ~(size_t)255 : 0;
+    pl->total_ws = 256 /* error word + counters */ + pl->list_bytes + pl->gmem_scratch;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_workspace_size(pscl_code c, int n_frames, int L, pscl_algo algo, const pscl_pruning *pr,
+                                   pscl_quant quant, size_t *bytes)
+{
+    if (!bytes) return fail(PSCL_EINVAL, "bytes is NULL");
+    Plan pl;
+    int rc = make_plan(c, n_frames, L, algo, pr, quant, &pl);
+    if (rc) return rc;
+    *bytes = pl.total_ws;
+    return PSCL_OK;
+}
+
+static cudaError_t launch_stage(int quant, const KParams &kp, int grid, size_t smem, cudaStream_t s)
+{
+    if (quant == PSCL_F32) return launch_scl_f32(kp, grid, 32 * kWarpsPerBlock, smem, s);
+    if (quant == PSCL_I16) return launch_scl_i16(kp, grid, 32 * kWarpsPerBlock, smem, s);
+    return launch_scl_i8(kp, grid, 32 * kWarpsPerBlock, smem, s);
+}
+
+static int g_last_launches = 0;
+
+static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_algo algo, const pscl_pruning *pr,
+                      pscl_quant quant, uint8_t *info_out, int32_t *status_out, float *pm_out, void *ws,
+                      size_t ws_bytes, cudaStream_t stream, const Plan &pl)
+{
+    if (n_frames == 0) return PSCL_OK;
+    if (!llr || !info_out || !status_out) return fail(PSCL_EINVAL, "llr, info_out and status_out are required");
+    if (ws_bytes < pl.total_ws || !ws) return fail(PSCL_EINVAL, "workspace too small: %zu < %zu", ws_bytes, pl.total_ws);
+    if (((uintptr_t)ws) & 255u) return fail(PSCL_EINVAL, "workspace must be 256-byte aligned");
+    char *w = (char *)ws;
+    uint32_t *err = (uint32_t *)w;
+    int32_t *counts = (int32_t *)(w + 64);  // two list counters
+    int32_t *lists = (int32_t *)(w + 256);
+    char *gmem = w + 256 + pl.list_bytes;
+    DevProps dp;
+    int rc = get_props(&dp);
+    if (rc) return rc;
+    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
+    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
+    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    int launches = 0;
+    for (int s = 0; s < pl.n_stages; s++) {
+        const int Ls = pl.stages[s];
+        KParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.code = c->dc;
+        kp.ops = pl.pg.d_ops;
+        kp.n_ops = pl.pg.n_ops;
+        kp.root_special = pl.pg.root_special;
+        make_layout(c, pl.pg, Ls, (int)quant, budget, &kp.lay);
+        kp.llr = llr;
+        kp.n_frames = n_frames;
+        kp.L = Ls;
+        kp.L_out = L;
+        kp.stage_L = Ls;
+        kp.info_out = info_out;
+        kp.status_out = status_out;
+        kp.pm_out = pm_out;
+        kp.gmem = gmem;
+        kp.total_warps = pl.total_warps;
+        kp.err = err;
+        const bool last = s == pl.n_stages - 1;
+        if (s == 0) {
+            kp.frame_list = nullptr;
+            kp.list_count = nullptr;
+        } else {
+            kp.frame_list = lists + (size_t)((s - 1) & 1) * (size_t)n_frames;
+            kp.list_count = counts + ((s - 1) & 1);
+        }
+        if (!last) {
+            kp.next_list = lists + (size_t)(s & 1) * (size_t)n_frames;
+            kp.next_count = counts + (s & 1);
+            CU(cudaMemsetAsync(kp.next_count, 0, sizeof(int32_t), stream));
+        }
+        const size_t smem = (size_t)kp.lay.smem_per_warp * kWarpsPerBlock;
+        cudaError_t e = launch_stage((int)quant, kp, pl.grid, smem, stream);
+        if (e != cudaSuccess) return fail(PSCL_ECUDA, "decode launch: %s", cudaGetErrorString(e));
+        launches++;
+    }
+    g_last_launches = launches;
+    return PSCL_OK;
+}
+
+// library-owned workspace, one per device, grown on demand
+static std::map<int, std::pair<void *, size_t>> g_ws;
+
+extern "C" int pscl_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_algo algo,
+                           const pscl_pruning *pr, pscl_quant quant, uint8_t *info_out, int32_t *status_out,
+                           float *pm_out, void *stream)
+{
+    Plan pl;
+    int rc = make_plan(c, n_frames, L, algo, pr, quant, &pl);
+    if (rc) return rc;
+    int dev;
+    CU(cudaGetDevice(&dev));
+    void *ws;
+    size_t wsb;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto &slot = g_ws[dev];
+        if (slot.second < pl.total_ws) {
+            if (slot.first) {
+                CU(cudaDeviceSynchronize());
+                CU(cudaFree(slot.first));
+                slot.first = nullptr;
+                slot.second = 0;
+            }
+            size_t want = pl.total_ws + pl.total_ws / 4;
+            CU(cudaMalloc(&slot.first, want));
+            CU(cudaMemset(slot.first, 0, 256));
+            slot.second = want;
+        }
+        ws = slot.first;
+        wsb = slot.second;
+    }
+    return run_decode(c, llr, n_frames, L, algo, pr, quant, info_out, status_out, pm_out, ws, wsb,
+                      (cudaStream_t)stream, pl);
+}
+
+extern "C" int pscl_decode_ws(pscl_code c, const float *llr, int n_frames, int L, pscl_algo algo,
+                              const pscl_pruning *pr, pscl_quant quant, uint8_t *info_out, int32_t *status_out,
+                              float *pm_out, void *workspace, size_t workspace_bytes, void *stream)
+{
+    Plan pl;
+    int rc = make_plan(c, n_frames, L, algo, pr, quant, &pl);
+    if (rc) return rc;
+    return run_decode(c, llr, n_frames, L, algo, pr, quant, info_out, status_out, pm_out, workspace,
+                      workspace_bytes, (cudaStream_t)stream, pl);
+}
+
+extern "C" int pscl_encode(pscl_code c, const uint8_t *info, int n_frames, uint8_t *x_out, void *stream)
+{
+    if (!c) return fail(PSCL_EINVAL, "code is NULL");
+    if (n_frames < 0) return fail(PSCL_EINVAL, "n_frames=%d", n_frames);
+    if (n_frames == 0) return PSCL_OK;
+    if (!info || !x_out) return fail(PSCL_EINVAL, "info and x_out are required");
+    EncParams p;
+    p.code = c->dc;
+    p.info = info;
+    p.x = x_out;
+    p.n_frames = n_frames;
+    cudaError_t e = launch_encode(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(PSCL_ECUDA, "encode launch: %s", cudaGetErrorString(e));
+    return PSCL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics used by the tests and the benchmark (not part of the paper's
+// method): kernel launches of the last decode call, the debug error word of
+// the library workspace (bounds-checked builds), and the tuning knob.
+extern "C" int pscl_debug_last_launches(void) { return g_last_launches; }
+
+extern "C" int pscl_debug_error_word(uint32_t *out)
+{
+    int dev;
+    CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find(dev);
+    *out = 0;
+    if (it == g_ws.end() || !it->second.first) return PSCL_OK;
+    CU(cudaMemcpy(out, it->second.first, 4, cudaMemcpyDeviceToHost));
+    return PSCL_OK;
+}
+
+extern "C" int pscl_set_tuning(int target_warps_per_sm)
+{
+    if (target_warps_per_sm < 1 || target_warps_per_sm > 64) return fail(PSCL_EINVAL, "target warps per SM out of range");
+    g_target_warps_per_sm = target_warps_per_sm;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_debug_checked(void)
+{
+#ifdef PSCL_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}

@@ -1,0 +1,99 @@
+// internal.h -- structures shared by the host side of libpolarscl and its
+// kernels.  Not part of the public ABI (see include/polarscl.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pscl {
+
+constexpr int kMaxLog2N = 11;          // N <= 2048
+constexpr int kMaxLayers = kMaxLog2N + 1;
+
+// One instruction of the node schedule a warp walks for a code (the
+// pre-order traversal of Algorithm 1, with pruned nodes as single steps).
+//   bits 0..3  opcode      bits 4..7  depth d      bits 8..10 node type
+//   bit  11    side (0 = left child, 1 = right child or root)
+//   bits 12..15 flip depth t
+enum Opcode : uint32_t {
+    OP_F = 0,     // layer d+1 = f(layer d)               (left child LLRs)
+    OP_G = 1,     // layer d+1 = g(layer d, beta_left)     (right child LLRs)
+    OP_NODE = 2,  // leaf or pruned node at depth d
+    OP_COMB = 3,  // right child at depth d done: parent beta = h(left, right)
+};
+enum NodeType : uint32_t { NT_R0 = 1, NT_R1 = 2, NT_REP = 3, NT_SPC = 4 };
+
+__host__ __device__ inline uint32_t op_make(uint32_t code, uint32_t d, uint32_t type, uint32_t side,
+                                            uint32_t t)
+{
+    return code | (d << 4) | (type << 8) | (side << 11) | (t << 12);
+}
+__host__ __device__ inline uint32_t op_code(uint32_t w) { return w & 15u; }
+__host__ __device__ inline int op_depth(uint32_t w) { return (int)((w >> 4) & 15u); }
+__host__ __device__ inline uint32_t op_type(uint32_t w) { return (w >> 8) & 7u; }
+__host__ __device__ inline int op_side(uint32_t w) { return (int)((w >> 11) & 1u); }
+__host__ __device__ inline int op_t(uint32_t w) { return (int)((w >> 12) & 15u); }
+
+// Device-resident description of a code.
+struct DevCode {
+    int N, n, K, kinfo, crc_len, systematic, P;
+    uint32_t poly32;            // crc_poly << (32 - crc_len)
+    const int32_t *in_index;    // N: column of position i in an LLR row, -1 if punctured
+    const uint16_t *A;          // K information positions, increasing
+    const uint32_t *amask;      // max(1, N/32) words: bit set for positions in A
+    const uint32_t *crc_lut;    // 256 entries, MSB-first table for the 32-bit-aligned CRC
+};
+
+// Per-warp memory map.  Offsets are bytes inside the warp's shared-memory
+// slice (bit d of *_smem set) or inside its global scratch slice.
+struct Layout {
+    uint32_t llr_off[kMaxLayers];
+    uint32_t llr_words[kMaxLayers];  // capacity in 32-bit words (bounds)
+    uint32_t bl_off[kMaxLayers];
+    uint32_t br_off[kMaxLayers];
+    uint32_t b_words[kMaxLayers];    // capacity of one beta buffer in words
+    uint32_t llr_smem, bl_smem, br_smem;
+    uint32_t src_off;                // shared: selection scatter area (64 words)
+    uint32_t ns_off;                 // global: non-systematic transform scratch
+    uint32_t ns_words;
+    uint32_t smem_per_warp;
+    uint32_t gmem_per_warp;
+};
+
+struct KParams {
+    DevCode code;
+    const uint32_t *ops;
+    int n_ops;
+    int root_special;
+    Layout lay;
+    const float *llr;
+    int n_frames;               // frames in the batch (rows of llr / outputs)
+    int L;                      // list size of this stage
+    int L_out;                  // pm_out row length
+    int stage_L;                // reported in status bits 8..15
+    const int32_t *frame_list;  // NULL: frames 0..n_frames-1; else frame ids
+    const int32_t *list_count;  // with frame_list: device count of ids
+    int32_t *next_list;         // adaptive: failed frames are appended here
+    int32_t *next_count;        //   (NULL when this is the last stage)
+    uint8_t *info_out;
+    int32_t *status_out;
+    float *pm_out;
+    char *gmem;                 // global scratch base
+    int total_warps;
+    uint32_t *err;              // debug error word (checked builds)
+};
+
+// launchers, one per number format (defined in scl_*.cu)
+cudaError_t launch_scl_f32(const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_scl_i16(const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_scl_i8(const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t scl_func_attrs(int quant, size_t smem, int block, int *blocks_per_sm);
+
+struct EncParams {
+    DevCode code;
+    const uint8_t *info;
+    uint8_t *x;
+    int n_frames;
+};
+cudaError_t launch_encode(const EncParams &p, cudaStream_t s);
+
+}  // namespace pscl

@@ -1,0 +1,42 @@
+// scl_f32.cu -- instantiation of the SCL kernel for the f32 number format.
+#include <map>
+#include <mutex>
+
+#include "scl_kernel.cuh"
+
+namespace pscl {
+
+static std::mutex g_attr_mu_f32;
+static std::map<int, bool> g_attr_set_f32;
+
+static cudaError_t ensure_attr_f32()
+{
+    int dev;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu_f32);
+    if (g_attr_set_f32[dev]) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(scl_kernel<QF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) g_attr_set_f32[dev] = true;
+    return e;
+}
+
+cudaError_t launch_scl_f32(const KParams &p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = ensure_attr_f32();
+    if (e != cudaSuccess) return e;
+    scl_kernel<QF32><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t scl_attrs_f32(size_t smem, int block, int *bps)
+{
+    cudaError_t e = ensure_attr_f32();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QF32>, block, smem);
+}
+
+}  // namespace pscl

@@ -1,0 +1,42 @@
+// scl_i16.cu -- instantiation of the SCL kernel for the i16 number format.
+#include <map>
+#include <mutex>
+
+#include "scl_kernel.cuh"
+
+namespace pscl {
+
+static std::mutex g_attr_mu_i16;
+static std::map<int, bool> g_attr_set_i16;
+
+static cudaError_t ensure_attr_i16()
+{
+    int dev;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu_i16);
+    if (g_attr_set_i16[dev]) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(scl_kernel<QI16>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) g_attr_set_i16[dev] = true;
+    return e;
+}
+
+cudaError_t launch_scl_i16(const KParams &p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = ensure_attr_i16();
+    if (e != cudaSuccess) return e;
+    scl_kernel<QI16><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t scl_attrs_i16(size_t smem, int block, int *bps)
+{
+    cudaError_t e = ensure_attr_i16();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QI16>, block, smem);
+}
+
+}  // namespace pscl

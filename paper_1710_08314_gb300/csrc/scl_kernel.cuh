@@ -1,0 +1,842 @@
+// scl_kernel.cuh -- the batched SCL decoding kernel (sm_103a).
+//
+// One warp decodes 32/L frames at once: lane = frame-in-warp * L + path slot.
+// Every lane runs the same node schedule (the pre-order traversal of
+// Algorithm 1 with pruned nodes collapsed), so control flow is uniform.
+//
+// Memory of a warp (Layout):
+//  - LLR layer d (d >= 1) holds, for every lane, the 2^(n-d) LLRs of the
+//    current depth-d node: row r, column lane, so the 32 lanes of a row are
+//    one 128-byte line.  Reads go to the column of the slot the path's layer
+//    was written by (lazy path copy by index indirection: a new path inherits
+//    its parent's per-layer slot table and writes only its own column).
+//  - layer 0 holds the channel LLRs of the warp's frames, column = frame.
+//  - BL_d / BR_d hold, bit-packed, the partial sums (Sec. II-B h) of the last
+//    completed left / right child at depth d; BL_d is indexed like the LLR
+//    layers, BR_d is always the lane's own column.
+//  - fixed point packs 2 (int16) or 4 (int8) LLRs per 32-bit word and runs f
+//    and g with SIMD-in-word intrinsics.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace pscl {
+
+#define PSCL_FULL 0xFFFFFFFFu
+
+// ---------------------------------------------------------------------------
+// Number formats.  Words hold EPW elements of BITS bits; V is the scalar type
+// handlers work in.  f and g follow Sec. II-B:
+//   f(a, b) = sign(a b) min(|a|, |b|)      g(a, b, s) = (1 - 2s) a + b
+// with the sign of f taken from the sign bits and g computed as (s?-a:a)+b.
+struct QF32 {
+    static constexpr int EPW = 1, BITS = 32, FIXED = 0;
+    typedef float V;
+    __device__ static __forceinline__ uint32_t F(uint32_t a, uint32_t b)
+    {
+        uint32_t m = __float_as_uint(fminf(fabsf(__uint_as_float(a)), fabsf(__uint_as_float(b))));
+        return m | ((a ^ b) & 0x80000000u);
+    }
+    // s: bit 0 = partial sum of the element
+    __device__ static __forceinline__ uint32_t G(uint32_t a, uint32_t b, uint32_t s)
+    {
+        return __float_as_uint(__fadd_rn(__uint_as_float(a ^ (s << 31)), __uint_as_float(b)));
+    }
+    __device__ static __forceinline__ V elem(uint32_t w, int) { return __uint_as_float(w); }
+    __device__ static __forceinline__ V absv(V v) { return fabsf(v); }
+    __device__ static __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
+    __device__ static __forceinline__ uint32_t key(V v) { return __float_as_uint(v); }
+    __device__ static __forceinline__ V from_key(uint32_t k) { return __uint_as_float(k); }
+    __device__ static __forceinline__ V zero() { return 0.0f; }
+    __device__ static __forceinline__ V big() { return __uint_as_float(0x7F800000u); }
+    __device__ static __forceinline__ uint32_t quant(float x) { return __float_as_uint(x); }
+    __device__ static __forceinline__ float to_float(V v) { return v; }
+    __device__ static __forceinline__ V sub(V a, V) { return a; }
+};
+
+struct QI16 {
+    static constexpr int EPW = 2, BITS = 16, FIXED = 1, Q = 32767, FRAC = 5;
+    typedef int V;
+    __device__ static __forceinline__ uint32_t F(uint32_t a, uint32_t b)
+    {
+        uint32_t m = __vminu2(__vabsss2(a), __vabsss2(b));
+        uint32_t mask = (((a ^ b) & 0x80008000u) >> 15) * 0xFFFFu;
+        return (m & ~mask) | (__vneg2(m) & mask);
+    }
+    // s: bits 0..1 = partial sums of the two elements
+    __device__ static __forceinline__ uint32_t G(uint32_t a, uint32_t b, uint32_t s)
+    {
+        uint32_t mask = ((s & 1u) * 0xFFFFu) | (((s >> 1) & 1u) * 0xFFFF0000u);
+        uint32_t na = (a & ~mask) | (__vneg2(a) & mask);
+        return __vmaxs2(__vaddss2(na, b), 0x80018001u);  // saturate to [-Q, Q]
+    }
+    __device__ static __forceinline__ V elem(uint32_t w, int k) { return (int)(int16_t)(w >> (16 * k)); }
+    __device__ static __forceinline__ V absv(V v) { return v < 0 ? -v : v; }
+    __device__ static __forceinline__ V add(V a, V b) { int s = a + b; return s > Q ? Q : s; }
+    __device__ static __forceinline__ uint32_t key(V v) { return (uint32_t)v; }
+    __device__ static __forceinline__ V from_key(uint32_t k) { return (int)k; }
+    __device__ static __forceinline__ V zero() { return 0; }
+    __device__ static __forceinline__ V big() { return 0x7FFFFFFF; }
+    __device__ static __forceinline__ uint32_t quant(float x)
+    {
+        float y = fminf(fmaxf(x * 32.0f, -32767.0f), 32767.0f);
+        return (uint32_t)__float2int_rn(y) & 0xFFFFu;
+    }
+    __device__ static __forceinline__ float to_float(V v) { return (float)v; }
+    __device__ static __forceinline__ V sub(V a, V b) { return a - b; }
+};
+
+struct QI8 {
+    static constexpr int EPW = 4, BITS = 8, FIXED = 1, Q = 127, FRAC = 2;
+    typedef int V;
+    __device__ static __forceinline__ uint32_t F(uint32_t a, uint32_t b)
+    {
+        uint32_t m = __vminu4(__vabsss4(a), __vabsss4(b));
+        uint32_t mask = (((a ^ b) & 0x80808080u) >> 7) * 0xFFu;
+        return (m & ~mask) | (__vneg4(m) & mask);
+    }
+    // s: bits 0..3 = partial sums of the four elements
+    __device__ static __forceinline__ uint32_t G(uint32_t a, uint32_t b, uint32_t s)
+    {
+        uint32_t mask = (((s & 15u) * 0x00204081u) & 0x01010101u) * 0xFFu;
+        uint32_t na = (a & ~mask) | (__vneg4(a) & mask);
+        return __vmaxs4(__vaddss4(na, b), 0x81818181u);  // saturate to [-Q, Q]
+    }
+    __device__ static __forceinline__ V elem(uint32_t w, int k) { return (int)(int8_t)(w >> (8 * k)); }
+    __device__ static __forceinline__ V absv(V v) { return v < 0 ? -v : v; }
+    __device__ static __forceinline__ V add(V a, V b) { int s = a + b; return s > Q ? Q : s; }
+    __device__ static __forceinline__ uint32_t key(V v) { return (uint32_t)v; }
+    __device__ static __forceinline__ V from_key(uint32_t k) { return (int)k; }
+    __device__ static __forceinline__ V zero() { return 0; }
+    __device__ static __forceinline__ V big() { return 0x7FFFFFFF; }
+    __device__ static __forceinline__ uint32_t quant(float x)
+    {
+        float y = fminf(fmaxf(x * 4.0f, -127.0f), 127.0f);
+        return (uint32_t)__float2int_rn(y) & 0xFFu;
+    }
+    __device__ static __forceinline__ float to_float(V v) { return (float)v; }
+    __device__ static __forceinline__ V sub(V a, V b) { return a - b; }
+};
+
+// ---------------------------------------------------------------------------
+// Warp context
+struct Ctx {
+    const KParams *P;
+    char *sm;        // warp's shared slice
+    char *gm;        // warp's global scratch slice
+    int lane, L, seg, slot, fpw, fiw;
+    int N, n;
+    int n_active;    // warp-uniform
+    uint32_t idxL[2], idxS[2];  // per-layer slot tables, 6 x 5 bits per word
+};
+
+__device__ __forceinline__ int tab_get(const uint32_t (&t)[2], int d)
+{
+    uint32_t w = d < 6 ? t[0] : t[1];
+    int sh = 5 * (d < 6 ? d : d - 6);
+    return (int)((w >> sh) & 31u);
+}
+__device__ __forceinline__ void tab_set(uint32_t (&t)[2], int d, int v)
+{
+    int sh = 5 * (d < 6 ? d : d - 6);
+    uint32_t m = ~(31u << sh);
+    if (d < 6) t[0] = (t[0] & m) | ((uint32_t)v << sh);
+    else t[1] = (t[1] & m) | ((uint32_t)v << sh);
+}
+__device__ __forceinline__ void tab_fill(uint32_t (&t)[2], int v)
+{
+    uint32_t w = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w |= (uint32_t)v << (5 * k);
+    t[0] = w;
+    t[1] = w;
+}
+
+#ifdef PSCL_CHECKED
+__device__ __forceinline__ bool chk(const Ctx &c, bool ok, uint32_t code)
+{
+    if (!ok) atomicOr(c.P->err, code);
+    return ok;
+}
+#define PSCL_OK_IDX(c, idx, cap, code) chk(c, (uint32_t)(idx) < (uint32_t)(cap), code)
+#else
+#define PSCL_OK_IDX(c, idx, cap, code) true
+#endif
+
+__device__ __forceinline__ uint32_t *llr_layer(const Ctx &c, int d)
+{
+    char *b = ((c.P->lay.llr_smem >> d) & 1u) ? c.sm : c.gm;
+    return (uint32_t *)(b + c.P->lay.llr_off[d]);
+}
+__device__ __forceinline__ uint32_t *bl_layer(const Ctx &c, int d)
+{
+    char *b = ((c.P->lay.bl_smem >> d) & 1u) ? c.sm : c.gm;
+    return (uint32_t *)(b + c.P->lay.bl_off[d]);
+}
+__device__ __forceinline__ uint32_t *br_layer(const Ctx &c, int d)
+{
+    char *b = ((c.P->lay.br_smem >> d) & 1u) ? c.sm : c.gm;
+    return (uint32_t *)(b + c.P->lay.br_off[d]);
+}
+
+__device__ __forceinline__ uint32_t ld(const Ctx &c, const uint32_t *p, int idx, uint32_t cap, uint32_t code)
+{
+    if (!PSCL_OK_IDX(c, idx, cap, code)) return 0u;
+    return p[idx];
+}
+__device__ __forceinline__ void st(const Ctx &c, uint32_t *p, int idx, uint32_t cap, uint32_t v, uint32_t code)
+{
+    if (!PSCL_OK_IDX(c, idx, cap, code)) return;
+    p[idx] = v;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src)
+{
+    uint32_t lo = __shfl_sync(PSCL_FULL, (uint32_t)v, src);
+    uint32_t hi = __shfl_sync(PSCL_FULL, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t shfl64_xor(uint64_t v, int m)
+{
+    uint32_t lo = __shfl_xor_sync(PSCL_FULL, (uint32_t)v, m);
+    uint32_t hi = __shfl_xor_sync(PSCL_FULL, (uint32_t)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// ---------------------------------------------------------------------------
+// f step at depth d: layer d+1 (own column) = f(layer d) for the left child.
+template <class Qt>
+__device__ __forceinline__ void op_f(Ctx &c, int d)
+{
+    const int S = c.N >> d, H = S >> 1;
+    const uint32_t *in = llr_layer(c, d);
+    uint32_t *out = llr_layer(c, d + 1);
+    const uint32_t cap_in = c.P->lay.llr_words[d], cap_out = c.P->lay.llr_words[d + 1];
+    const int win = d == 0 ? c.fpw : 32;
+    const int cin = d == 0 ? c.fiw : c.seg + tab_get(c.idxL, d);
+    if (H >= Qt::EPW) {
+        const int HW = H / Qt::EPW;
+#pragma unroll 4
+        for (int w = 0; w < HW; ++w) {
+            uint32_t a = ld(c, in, w * win + cin, cap_in, 1u);
+            uint32_t b = ld(c, in, (w + HW) * win + cin, cap_in, 1u);
+            st(c, out, w * 32 + c.lane, cap_out, Qt::F(a, b), 2u);
+        }
+    } else {
+        uint32_t wd = ld(c, in, cin, cap_in, 1u);
+        st(c, out, c.lane, cap_out, Qt::F(wd, wd >> (H * Qt::BITS)), 2u);
+    }
+    tab_set(c.idxL, d + 1, c.slot);
+}
+
+// g step at depth d: layer d+1 (own column) = g(layer d, beta of the left
+// child, stored in BL_{d+1}).
+template <class Qt>
+__device__ __forceinline__ void op_g(Ctx &c, int d)
+{
+    const int S = c.N >> d, H = S >> 1;
+    const uint32_t *in = llr_layer(c, d);
+    uint32_t *out = llr_layer(c, d + 1);
+    const uint32_t *bl = bl_layer(c, d + 1);
+    const uint32_t cap_in = c.P->lay.llr_words[d], cap_out = c.P->lay.llr_words[d + 1];
+    const uint32_t cap_b = c.P->lay.b_words[d + 1];
+    const int win = d == 0 ? c.fpw : 32;
+    const int cin = d == 0 ? c.fiw : c.seg + tab_get(c.idxL, d);
+    const int cs = c.seg + tab_get(c.idxS, d + 1);
+    if (H >= Qt::EPW) {
+        const int HW = H / Qt::EPW;
+        constexpr int WPB = 32 / Qt::EPW;  // LLR words per 32-bit beta word
+        for (int w0 = 0; w0 < HW; w0 += WPB) {
+            uint32_t bw = ld(c, bl, (w0 / WPB) * 32 + cs, cap_b, 4u);
+            const int cnt = HW - w0 < WPB ? HW - w0 : WPB;
+#pragma unroll 4
+            for (int k = 0; k < cnt; ++k) {
+                const int w = w0 + k;
+                uint32_t a = ld(c, in, w * win + cin, cap_in, 1u);
+                uint32_t b = ld(c, in, (w + HW) * win + cin, cap_in, 1u);
+                uint32_t s = (bw >> (k * Qt::EPW)) & ((1u << Qt::EPW) - 1u);
+                st(c, out, w * 32 + c.lane, cap_out, Qt::G(a, b, s), 2u);
+            }
+        }
+    } else {
+        uint32_t wd = ld(c, in, cin, cap_in, 1u);
+        uint32_t s = ld(c, bl, cs, cap_b, 4u) & ((1u << H) - 1u);
+        st(c, out, c.lane, cap_out, Qt::G(wd, wd >> (H * Qt::BITS), s), 2u);
+    }
+    tab_set(c.idxL, d + 1, c.slot);
+}
+
+// h step: the right child at depth d is complete (its beta in BR_d); the
+// parent's beta (BL_d ^ BR_d, BR_d) goes to BL_{d-1} (parent is a left
+// child) or BR_{d-1}.
+__device__ __forceinline__ void op_comb(Ctx &c, int d, int parent_side)
+{
+    const int S = c.N >> d;
+    const uint32_t *bl = bl_layer(c, d);
+    const uint32_t *br = br_layer(c, d);
+    uint32_t *dst = parent_side == 0 ? bl_layer(c, d - 1) : br_layer(c, d - 1);
+    const uint32_t cap = c.P->lay.b_words[d], capd = c.P->lay.b_words[d - 1];
+    const int cl = c.seg + tab_get(c.idxS, d);
+    if (S >= 32) {
+        const int W = S >> 5;
+        for (int w = 0; w < W; ++w) {
+            uint32_t l = ld(c, bl, w * 32 + cl, cap, 8u);
+            uint32_t r = ld(c, br, w * 32 + c.lane, cap, 8u);
+            st(c, dst, w * 32 + c.lane, capd, l ^ r, 16u);
+            st(c, dst, (w + W) * 32 + c.lane, capd, r, 16u);
+        }
+    } else {
+        const uint32_t m = (1u << S) - 1u;
+        uint32_t l = ld(c, bl, cl, cap, 8u);
+        uint32_t r = ld(c, br, c.lane, cap, 8u) & m;
+        st(c, dst, c.lane, capd, ((l ^ r) & m) | (r << S), 16u);
+    }
+    if (parent_side == 0) tab_set(c.idxS, d - 1, c.slot);
+}
+
+// ---------------------------------------------------------------------------
+// Balanced pairwise sum over index order, fed one element at a time: the
+// binary-counter form adds acc[l] + v exactly where the recursive tree
+// s(lo, hi) = s(lo, mid) + s(mid, hi) would.  Returns the value stored at the
+// last push (the full sum after the last element of a power-of-two run).
+template <class Qt>
+struct TreeSum {
+    typename Qt::V acc[kMaxLayers];
+    __device__ __forceinline__ typename Qt::V push(typename Qt::V v, int i)
+    {
+#pragma unroll
+        for (int l = 0; l < kMaxLayers; ++l) {
+            if ((i >> l) & 1) {
+                v = Qt::add(acc[l], v);
+            } else {
+                acc[l] = v;
+                return v;
+            }
+        }
+        return v;
+    }
+};
+
+// segment-wide minimum of the metrics of active slots (fixed point only)
+template <class Qt>
+__device__ __forceinline__ void normalise(Ctx &c, typename Qt::V &pm)
+{
+    if (!Qt::FIXED) return;
+    typename Qt::V v = c.slot < c.n_active ? pm : Qt::big();
+    for (int m = 1; m < c.L; m <<= 1) {
+        typename Qt::V o = __shfl_xor_sync(PSCL_FULL, v, m);
+        v = o < v ? o : v;
+    }
+    pm = Qt::sub(pm, v);
+}
+
+// Bitonic sort (ascending) of the L*M keys of a segment; element e = slot*M + m.
+template <int M>
+__device__ __forceinline__ void bitonic_seg(uint64_t (&k)[M], int L, int slot)
+{
+    const int E = L * M;
+    for (int size = 2; size <= E; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= M) {
+                const int ls = stride / M;
+                const bool lower = (slot & ls) == 0;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const int e = slot * M + m;
+                    const bool up = (e & size) == 0;
+                    uint64_t o = shfl64_xor(k[m], ls);
+                    const bool takemin = lower == up;
+                    uint64_t mn = o < k[m] ? o : k[m];
+                    uint64_t mx = o < k[m] ? k[m] : o;
+                    k[m] = takemin ? mn : mx;
+                }
+            } else {
+#pragma unroll
+                for (int sb = 0; (1 << sb) < M; ++sb) {
+                    if (stride == (1 << sb)) {
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            if ((m & (1 << sb)) == 0) {
+                                const int mp = m | (1 << sb);
+                                const int e = slot * M + m;
+                                const bool up = (e & size) == 0;
+                                uint64_t a = k[m], b = k[mp];
+                                if ((a > b) == up) {
+                                    k[m] = b;
+                                    k[mp] = a;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Keep the min(L, n_active*M) smallest (PM, c) candidates, c = slot*M + m,
+// and give them new slots in increasing c.  kp[m] is the ordered bit pattern
+// of candidate m's metric.  On return, lanes with slot < n_keep know their
+// parent slot, candidate index and metric key.
+template <int M>
+__device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], int &par, int &cand,
+                                             uint32_t &newkey, int &n_keep)
+{
+    const int na = c.n_active;
+    const int n_cand = na * M;
+    if (n_cand <= c.L) {
+        n_keep = n_cand;
+        par = c.slot < n_keep ? c.slot / M : 0;
+        cand = c.slot < n_keep ? c.slot % M : 0;
+        uint32_t v = 0;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            uint32_t x = __shfl_sync(PSCL_FULL, kp[m], c.seg + par);
+            if (m == cand) v = x;
+        }
+        newkey = v;
+        return;
+    }
+    n_keep = c.L;
+    uint64_t k[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+        k[m] = c.slot < na ? (((uint64_t)kp[m] << 32) | (uint32_t)(c.slot * M + m)) : ~0ull;
+    bitonic_seg<M>(k, c.L, c.slot);
+    const int tp = (c.L - 1) / M, tm = (c.L - 1) % M;
+    uint64_t mine = 0;
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+        if (m == tm) mine = k[m];
+    const uint64_t tau = shfl64(mine, c.seg + tp);
+    int cnt = 0;
+    bool surv[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        uint64_t orig = c.slot < na ? (((uint64_t)kp[m] << 32) | (uint32_t)(c.slot * M + m)) : ~0ull;
+        surv[m] = orig <= tau;
+        cnt += surv[m] ? 1 : 0;
+    }
+    int incl = cnt;
+    for (int off = 1; off < c.L; off <<= 1) {
+        int y = __shfl_up_sync(PSCL_FULL, incl, off, c.L);
+        if (c.slot >= off) incl += y;
+    }
+    int r = incl - cnt;
+    uint32_t *src = (uint32_t *)(c.sm + c.P->lay.src_off);
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        if (surv[m]) {
+            if (PSCL_OK_IDX(c, c.seg + r, 32, 32u)) {
+                src[2 * (c.seg + r)] = ((uint32_t)c.slot << 8) | (uint32_t)m;
+                src[2 * (c.seg + r) + 1] = kp[m];
+            }
+            ++r;
+        }
+    }
+    __syncwarp();
+    const uint32_t e0 = src[2 * c.lane], e1 = src[2 * c.lane + 1];
+    __syncwarp();
+    par = (int)(e0 >> 8) & (c.L - 1);
+    cand = (int)(e0 & 255u);
+    if (cand >= M) cand = 0;
+    newkey = e1;
+}
+
+// ---------------------------------------------------------------------------
+// A leaf or pruned node at depth d (Sec. II-B; candidate rules as in the
+// header notes of the oracle and the ABI).
+template <class Qt, int M>
+__device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int side, int t,
+                                                   const uint32_t (&kp)[M], uint32_t h,
+                                                   const uint32_t (&rp)[3], typename Qt::V &pm)
+{
+    const int S = c.N >> d;
+    uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
+    const uint32_t capd = c.P->lay.b_words[d];
+    int par, cand, n_keep;
+    uint32_t newkey;
+    select_paths<M>(c, kp, par, cand, newkey, n_keep);
+    const int pl = c.seg + par;
+    // the new path inherits its parent's slot tables (lazy copy)
+    c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
+    c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
+    c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
+    c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
+    const uint32_t hp = __shfl_sync(PSCL_FULL, h, pl);
+    uint32_t r0 = __shfl_sync(PSCL_FULL, rp[0], pl);
+    uint32_t r1 = __shfl_sync(PSCL_FULL, rp[1], pl);
+    uint32_t r2 = __shfl_sync(PSCL_FULL, rp[2], pl);
+    pm = Qt::from_key(newkey);
+    if (type == NT_REP) {
+        const uint32_t ones = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
+        const int W = S >= 32 ? S >> 5 : 1;
+        for (int w = 0; w < W; ++w) st(c, dst, w * 32 + c.lane, capd, cand ? ones : 0u, 64u);
+    } else {
+        // R1 / SPC: parent's hard decisions with the candidate's flips
+        int j = cand;
+        if (type == NT_SPC) {
+            const int parity = S > 32 ? (int)((r2 >> 16) & 1u) : (__popc(hp) & 1);
+            j = (cand << 1) | ((__popc((unsigned)cand) & 1) ^ parity);
+        }
+        uint32_t pos[5] = {r0 & 0xFFFFu, r0 >> 16, r1 & 0xFFFFu, r1 >> 16, r2 & 0xFFFFu};
+        if (S <= 32) {
+            uint32_t b = hp;
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k < t && ((j >> k) & 1)) b ^= 1u << (pos[k] & 31u);
+            st(c, dst, c.lane, capd, b, 64u);
+        } else {
+            const int W = S >> 5;
+            for (int w = 0; w < W; ++w) {
+                uint32_t v = ld(c, dst, w * 32 + pl, capd, 128u);
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    if (k < t && ((j >> k) & 1) && (int)(pos[k] >> 5) == w) v ^= 1u << (pos[k] & 31u);
+                st(c, dst, w * 32 + c.lane, capd, v, 64u);
+                __syncwarp();
+            }
+        }
+    }
+    if (side == 0) tab_set(c.idxS, d, c.slot);
+    c.n_active = n_keep;
+    normalise<Qt>(c, pm);
+}
+
+template <class Qt>
+__device__ __noinline__ void op_node(Ctx &c, int d, int type, int side, int t, typename Qt::V &pm)
+{
+    typedef typename Qt::V V;
+    const int S = c.N >> d;
+    const uint32_t *in = llr_layer(c, d);
+    const uint32_t cap_in = c.P->lay.llr_words[d];
+    const int win = d == 0 ? c.fpw : 32;
+    const int cin = d == 0 ? c.fiw : c.seg + tab_get(c.idxL, d);
+    uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
+    const uint32_t capd = c.P->lay.b_words[d];
+
+    if (type == NT_R0 || type == NT_REP) {
+        TreeSum<Qt> t0, t1;
+        V p0 = Qt::zero(), p1 = Qt::zero();
+        const int nw = (S + Qt::EPW - 1) / Qt::EPW;
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t wd = ld(c, in, w * win + cin, cap_in, 1u);
+#pragma unroll
+            for (int e = 0; e < Qt::EPW; ++e) {
+                const int i = w * Qt::EPW + e;
+                if (i < S) {
+                    const V v = Qt::elem(wd, e);
+                    p0 = t0.push(v < 0 ? Qt::absv(v) : Qt::zero(), i);
+                    if (type == NT_REP) p1 = t1.push(v > 0 ? Qt::absv(v) : Qt::zero(), i);
+                }
+            }
+        }
+        if (type == NT_R0) {
+            pm = Qt::add(pm, p0);
+            const int W = S >= 32 ? S >> 5 : 1;
+            for (int w = 0; w < W; ++w) st(c, dst, w * 32 + c.lane, capd, 0u, 64u);
+            if (side == 0) tab_set(c.idxS, d, c.slot);
+            normalise<Qt>(c, pm);
+            return;
+        }
+        uint32_t kp[2] = {Qt::key(Qt::add(pm, p0)), Qt::key(Qt::add(pm, p1))};
+        uint32_t rp[3] = {0u, 0u, 0u};
+        node_select_finish<Qt, 2>(c, d, type, side, t, kp, 0u, rp, pm);
+        return;
+    }
+
+    // R1 / SPC: hard decisions, parity, and the t least reliable positions
+    V bv[5];
+    int bi[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        bv[k] = Qt::big();
+        bi[k] = 0;
+    }
+    uint32_t hword = 0, hlast = 0;
+    int parity = 0;
+    const int nw = (S + Qt::EPW - 1) / Qt::EPW;
+    for (int w = 0; w < nw; ++w) {
+        const uint32_t wd = ld(c, in, w * win + cin, cap_in, 1u);
+#pragma unroll
+        for (int e = 0; e < Qt::EPW; ++e) {
+            const int i = w * Qt::EPW + e;
+            if (i < S) {
+                const V v = Qt::elem(wd, e);
+                const V a = Qt::absv(v);
+                hword |= (uint32_t)(v < 0) << (i & 31);
+                if (a < bv[4]) {
+                    bool placed = false;
+#pragma unroll
+                    for (int k = 4; k >= 1; --k) {
+                        if (!placed) {
+                            if (a < bv[k - 1]) {
+                                bv[k] = bv[k - 1];
+                                bi[k] = bi[k - 1];
+                            } else {
+                                bv[k] = a;
+                                bi[k] = i;
+                                placed = true;
+                            }
+                        }
+                    }
+                    if (!placed) {
+                        bv[0] = a;
+                        bi[0] = i;
+                    }
+                }
+                if ((i & 31) == 31 || i == S - 1) {
+                    parity ^= __popc(hword) & 1;
+                    if (S > 32) st(c, dst, (i >> 5) * 32 + c.lane, capd, hword, 64u);
+                    hlast = hword;
+                    hword = 0;
+                }
+            }
+        }
+    }
+    uint32_t rp[3] = {(uint32_t)bi[0] | ((uint32_t)bi[1] << 16), (uint32_t)bi[2] | ((uint32_t)bi[3] << 16),
+                      (uint32_t)bi[4] | ((uint32_t)parity << 16)};
+    const uint32_t h = S <= 32 ? hlast : 0u;
+    // candidate penalties: left fold over flipped ranks (ascending)
+#define PSCL_CANDS(MM)                                                                   \
+    {                                                                                    \
+        uint32_t kp[MM];                                                                 \
+        _Pragma("unroll") for (int m = 0; m < MM; ++m)                                   \
+        {                                                                                \
+            int j = type == NT_R1 ? m : ((m << 1) | ((__popc((unsigned)m) & 1) ^ parity)); \
+            V pen = Qt::zero();                                                          \
+            _Pragma("unroll") for (int k = 0; k < 5; ++k) if (k < t && ((j >> k) & 1)) pen = \
+                Qt::add(pen, bv[k]);                                                     \
+            kp[m] = Qt::key(Qt::add(pm, pen));                                           \
+        }                                                                                \
+        node_select_finish<Qt, MM>(c, d, type, side, t, kp, h, rp, pm);                 \
+    }
+    const int M = type == NT_R1 ? (1 << t) : (1 << (t - 1));
+    switch (M) {
+    case 1: PSCL_CANDS(1) break;
+    case 2: PSCL_CANDS(2) break;
+    case 4: PSCL_CANDS(4) break;
+    case 8: PSCL_CANDS(8) break;
+    default: PSCL_CANDS(16) break;
+    }
+#undef PSCL_CANDS
+}
+
+// ---------------------------------------------------------------------------
+// codeword word w (32 positions) of the lane's path (or of slot `col`'s path
+// with its BL_1 column `cl`) once the root is complete
+__device__ __forceinline__ uint32_t xhat_word(const Ctx &c, int w, int col, int cl)
+{
+    const KParams &P = *c.P;
+    if (P.root_special) return ld(c, br_layer(c, 0), w * 32 + col, P.lay.b_words[0], 256u);
+    const int half = c.N >> 1;
+    const uint32_t *bl = bl_layer(c, 1), *br = br_layer(c, 1);
+    const uint32_t cap = P.lay.b_words[1];
+    if (half >= 32) {
+        const int W = half >> 5;
+        if (w < W) return ld(c, bl, w * 32 + cl, cap, 256u) ^ ld(c, br, w * 32 + col, cap, 256u);
+        return ld(c, br, (w - W) * 32 + col, cap, 256u);
+    }
+    const uint32_t m = (1u << half) - 1u;
+    const uint32_t l = ld(c, bl, cl, cap, 256u), r = ld(c, br, col, cap, 256u) & m;
+    return ((l ^ r) & m) | (r << half);
+}
+
+// word w of u = x F (non-systematic codes) for the lane's path: the
+// transform is an involution, applied here on the lane's scratch column
+static __device__ void nonsys_transform(const Ctx &c, int cl)
+{
+    const int NW = c.N >= 32 ? c.N >> 5 : 1;
+    uint32_t *ns = (uint32_t *)(c.gm + c.P->lay.ns_off);
+    const uint32_t cap = c.P->lay.ns_words;
+    for (int w = 0; w < NW; ++w) st(c, ns, w * 32 + c.lane, cap, xhat_word(c, w, c.lane, cl), 512u);
+    // strides >= 32 positions: whole words
+    for (int sw = NW >> 1; sw >= 1; sw >>= 1)
+        for (int w = 0; w < NW; ++w)
+            if ((w & sw) == 0) {
+                uint32_t a = ld(c, ns, w * 32 + c.lane, cap, 512u) ^ ld(c, ns, (w + sw) * 32 + c.lane, cap, 512u);
+                st(c, ns, w * 32 + c.lane, cap, a, 512u);
+            }
+    // strides < 32 inside each word: x_i ^= x_{i+s} for i with bit s clear
+    const int top = c.N < 32 ? c.N : 32;
+    for (int w = 0; w < NW; ++w) {
+        uint32_t v = ld(c, ns, w * 32 + c.lane, cap, 512u);
+        const uint32_t lo[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            if ((1 << k) < top) v ^= (v >> (1 << k)) & lo[k];
+        st(c, ns, w * 32 + c.lane, cap, v, 512u);
+    }
+}
+
+__device__ __forceinline__ uint32_t uword(const Ctx &c, int w, int col, int cl)
+{
+    if (c.P->code.systematic) return xhat_word(c, w, col, cl);
+    const uint32_t *ns = (const uint32_t *)(c.gm + c.P->lay.ns_off);
+    return ld(c, ns, w * 32 + col, c.P->lay.ns_words, 512u);
+}
+
+// CRC check of the lane's path (Sec. IV-A): bits of u_A in order, the first
+// K_info feed the CRC register (MSB first, 32-bit aligned), the last c are
+// compared with the remainder.
+static __device__ bool crc_check(const Ctx &c, int cl)
+{
+    const DevCode &cd = c.P->code;
+    if (cd.crc_len == 0) return true;
+    const int NW = c.N >= 32 ? c.N >> 5 : 1;
+    uint32_t reg = 0, recv = 0;
+    int k = 0;
+    for (int w = 0; w < NW; ++w) {
+        uint32_t am = __ldg(&cd.amask[w]);
+        if (!am) continue;
+        const uint32_t x = uword(c, w, c.lane, cl);
+        while (am) {
+            const int b = __ffs(am) - 1;
+            am &= am - 1u;
+            const uint32_t bit = (x >> b) & 1u;
+            if (k < cd.kinfo) {
+                const uint32_t top = reg >> 31;
+                reg <<= 1;
+                if (top ^ bit) reg ^= cd.poly32;
+            } else {
+                recv = (recv << 1) | bit;
+            }
+            ++k;
+        }
+    }
+    return (reg >> (32 - cd.crc_len)) == recv;
+}
+
+// ---------------------------------------------------------------------------
+// Decode the frames of one task: list positions [pos0, pos0 + 32/L).
+template <class Qt>
+__device__ void decode_task(Ctx &c, int pos0, int count)
+{
+    typedef typename Qt::V V;
+    const KParams &P = *c.P;
+    const DevCode &cd = P.code;
+    int32_t *fids = (int32_t *)(c.sm + P.lay.src_off) + 64;  // 32 frame ids
+    // frame id of this lane's frame (-1: none)
+    const int pos = pos0 + c.fiw;
+    int frame = -1;
+    if (pos < count) frame = P.frame_list ? __ldg(&P.frame_list[pos]) : pos;
+    if (c.slot == 0) fids[c.fiw] = frame;
+    __syncwarp();
+    // layer 0: channel LLRs of the warp's frames, quantised and packed
+    {
+        uint32_t *l0 = llr_layer(c, 0);
+        const uint32_t cap = P.lay.llr_words[0];
+        const int rows = (c.N + Qt::EPW - 1) / Qt::EPW;
+        const int stride = c.N - cd.P;
+        for (int wi = c.lane; wi < rows * c.fpw; wi += 32) {
+            const int row = wi / c.fpw, fr = wi - row * c.fpw;
+            const int f = fids[fr];
+            uint32_t word = 0;
+#pragma unroll
+            for (int e = 0; e < Qt::EPW; ++e) {
+                const int i = row * Qt::EPW + e;
+                float x = 0.0f;
+                if (i < c.N && f >= 0) {
+                    const int col = __ldg(&cd.in_index[i]);
+                    if (col >= 0) x = __ldg(&P.llr[(size_t)f * (size_t)stride + col]);
+                }
+                uint32_t q = Qt::quant(x);
+                word |= Qt::EPW == 1 ? q : (q << (e * Qt::BITS));
+            }
+            st(c, l0, row * c.fpw + fr, cap, word, 1024u);
+        }
+    }
+    __syncwarp();
+    c.n_active = 1;
+    tab_fill(c.idxL, c.slot);
+    tab_fill(c.idxS, c.slot);
+    V pm = Qt::zero();
+    // walk the node schedule
+    for (int i = 0; i < P.n_ops; ++i) {
+        const uint32_t op = __ldg(&P.ops[i]);
+        const int d = op_depth(op);
+        switch (op_code(op)) {
+        case OP_F: op_f<Qt>(c, d); break;
+        case OP_G: op_g<Qt>(c, d); break;
+        case OP_COMB: op_comb(c, d, op_side(op)); break;
+        default: op_node<Qt>(c, d, (int)op_type(op), op_side(op), op_t(op), pm); break;
+        }
+        __syncwarp();
+    }
+    // final selection (Sec. IV-A): best metric among paths passing the CRC
+    const int cl = c.seg + tab_get(c.idxS, 1);
+    if (!cd.systematic) {
+        nonsys_transform(c, cl);
+        __syncwarp();
+    }
+    const bool active = c.slot < c.n_active;
+    const bool ok = active && crc_check(c, cl);
+    uint64_t key = active ? (((uint64_t)(ok ? 0u : 1u) << 40) | ((uint64_t)Qt::key(pm) << 8) | (uint64_t)c.slot)
+                          : ~0ull;
+    for (int m = 1; m < c.L; m <<= 1) {
+        uint64_t o = shfl64_xor(key, m);
+        key = o < key ? o : key;
+    }
+    const int win = (int)(key & 0xFFu);
+    const bool wok = ((key >> 40) & 1u) == 0;
+    const int wcol = c.seg + win;
+    const int wcl = __shfl_sync(PSCL_FULL, cl, wcol);
+    if (frame >= 0) {
+        if (c.slot == 0) {
+            bool pass = wok;
+            if (!pass && P.next_list) {
+                const int at = atomicAdd(P.next_count, 1);
+                P.next_list[at] = frame;
+            }
+            P.status_out[frame] = (pass ? 1 : 0) | (P.stage_L << 8) | (win << 16);
+        }
+        if (P.pm_out) {
+            for (int s = c.slot; s < P.L_out; s += c.L)
+                P.pm_out[(size_t)frame * (size_t)P.L_out + s] = (s == c.slot && active) ? Qt::to_float(pm)
+                                                                                        : __uint_as_float(0x7F800000u);
+        }
+        const int nbytes = (cd.kinfo + 7) >> 3;
+        for (int b = c.slot; b < nbytes; b += c.L) {
+            uint32_t byte = 0;
+            for (int k = 0; k < 8; ++k) {
+                const int i = 8 * b + k;
+                if (i < cd.kinfo) {
+                    const int pz = __ldg(&cd.A[i]);
+                    const uint32_t wv = uword(c, pz >> 5, wcol, wcl);
+                    byte |= ((wv >> (pz & 31)) & 1u) << (7 - k);
+                }
+            }
+            P.info_out[(size_t)frame * (size_t)nbytes + b] = (uint8_t)byte;
+        }
+    }
+    __syncwarp();
+}
+
+template <class Qt>
+__global__ void __launch_bounds__(128) scl_kernel(const __grid_constant__ KParams P)
+{
+    extern __shared__ __align__(16) char smem[];
+    Ctx c;
+    c.P = &P;
+    const int warp = threadIdx.x >> 5;
+    c.lane = threadIdx.x & 31;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
+    c.sm = smem + (size_t)warp * P.lay.smem_per_warp;
+    c.gm = P.gmem + (size_t)gwarp * P.lay.gmem_per_warp;
+    c.L = P.L;
+    c.fpw = 32 / P.L;
+    c.slot = c.lane & (P.L - 1);
+    c.seg = c.lane - c.slot;
+    c.fiw = c.lane / P.L;
+    c.N = P.code.N;
+    c.n = P.code.n;
+    c.n_active = 1;
+    const int count = P.frame_list ? *P.list_count : P.n_frames;
+    const int n_tasks = (count + c.fpw - 1) / c.fpw;
+    for (int task = gwarp; task < n_tasks; task += P.total_warps) decode_task<Qt>(c, task * c.fpw, count);
+}
+
+}  // namespace pscl

@@ -1,0 +1,207 @@
+"""ctypes binding of libpolarscl (include/polarscl.h): same names, argument
+marshalling only.  Tensors are passed as device pointers; streams as the raw
+cudaStream_t of a torch stream.  There is no CPU fallback: if the library or
+CUDA is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+PSCL_OK, PSCL_EINVAL, PSCL_ENOMEM, PSCL_EUNSUPPORTED, PSCL_ECUDA, PSCL_ETIMEDOUT, PSCL_EAGAIN = 0, -1, -2, -3, -4, -5, -6
+PSCL_SC, PSCL_CASCL, PSCL_PASCL, PSCL_FASCL = 0, 1, 2, 3
+PSCL_F32, PSCL_I16, PSCL_I8 = 0, 1, 2
+PSCL_PRUNE_R0, PSCL_PRUNE_R1, PSCL_PRUNE_REP, PSCL_PRUNE_SPC = 1, 2, 4, 8
+
+ALGOS = {"sc": PSCL_SC, "cascl": PSCL_CASCL, "pascl": PSCL_PASCL, "fascl": PSCL_FASCL}
+QUANTS = {"f32": PSCL_F32, "i16": PSCL_I16, "i8": PSCL_I8}
+
+
+class pscl_pruning(C.Structure):
+    _fields_ = [("mask", C.c_uint32), ("rep_max", C.c_int), ("spc_max", C.c_int),
+                ("r1_t", C.c_int), ("spc_t", C.c_int), ("r1_max", C.c_int)]
+
+
+def pruning(mask=0, rep_max=0, spc_max=4, r1_t=2, spc_t=4, r1_max=0) -> pscl_pruning:
+    return pscl_pruning(mask, rep_max, spc_max, r1_t, spc_t, r1_max)
+
+
+class PsclError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"polarscl error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_libs: dict[str, C.CDLL] = {}
+
+
+def variant() -> str:
+    return "checked" if os.environ.get("PSCL_CHECKED", "0") == "1" else "release"
+
+
+def lib() -> C.CDLL:
+    v = variant()
+    with _lock:
+        if v not in _libs:
+            path = _build.lib_path(v)
+            if not os.path.exists(path) or os.environ.get("PSCL_AUTOBUILD", "1") == "1":
+                path = _build.build(v)
+            L = C.CDLL(path)
+            vp, i, u32 = C.c_void_p, C.c_int, C.c_uint32
+            L.pscl_create_code.argtypes = [i, i, vp, i, u32, vp, i, C.POINTER(vp)]
+            L.pscl_destroy_code.argtypes = [vp]
+            L.pscl_code_info.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)]
+            L.pscl_prepare.argtypes = [vp, vp]
+            L.pscl_decode.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
+            L.pscl_workspace_size.argtypes = [vp, i, i, i, vp, i, C.POINTER(C.c_size_t)]
+            L.pscl_decode_ws.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp, C.c_size_t, vp]
+            L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
+            L.pscl_last_error.restype = C.c_char_p
+            L.pscl_version.restype = C.c_char_p
+            L.pscl_debug_error_word.argtypes = [C.POINTER(u32)]
+            L.pscl_set_tuning.argtypes = [i]
+            _libs[v] = L
+        return _libs[v]
+
+
+def _check(rc):
+    if rc != PSCL_OK:
+        raise PsclError(rc, lib().pscl_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return C.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(int(t))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def pscl_last_error() -> str:
+    return lib().pscl_last_error().decode()
+
+
+def pscl_version() -> str:
+    return lib().pscl_version().decode()
+
+
+def pscl_create_code(N, K, frozen, crc_len, crc_poly, puncture=None, systematic=1):
+    """frozen / puncture: host numpy uint8 arrays of N entries."""
+    import numpy as np
+    fr = np.ascontiguousarray(np.asarray(frozen, dtype=np.uint8))
+    pu = None if puncture is None else np.ascontiguousarray(np.asarray(puncture, dtype=np.uint8))
+    h = C.c_void_p()
+    _check(lib().pscl_create_code(N, K, _ptr(fr), crc_len, crc_poly, _ptr(pu), int(systematic), C.byref(h)))
+    return h
+
+
+def pscl_destroy_code(code):
+    return _check(lib().pscl_destroy_code(code))
+
+
+def pscl_code_info(code):
+    N, K, Ki, P = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(lib().pscl_code_info(code, C.byref(N), C.byref(K), C.byref(Ki), C.byref(P)))
+    return N.value, K.value, Ki.value, P.value
+
+
+def pscl_prepare(code, prune=None):
+    return _check(lib().pscl_prepare(code, C.byref(prune) if prune is not None else None))
+
+
+def pscl_decode(code, llr, n_frames, L, algo, prune, quant, info_out, status_out, pm_out=None, stream=None):
+    return _check(lib().pscl_decode(code, _ptr(llr), n_frames, L, algo,
+                                    C.byref(prune) if prune is not None else None, quant,
+                                    _ptr(info_out), _ptr(status_out), _ptr(pm_out), _stream(stream)))
+
+
+def pscl_workspace_size(code, n_frames, L, algo, prune, quant) -> int:
+    b = C.c_size_t()
+    _check(lib().pscl_workspace_size(code, n_frames, L, algo, C.byref(prune) if prune is not None else None,
+                                     quant, C.byref(b)))
+    return b.value
+
+
+def pscl_decode_ws(code, llr, n_frames, L, algo, prune, quant, info_out, status_out, pm_out, workspace,
+                   workspace_bytes, stream=None):
+    return _check(lib().pscl_decode_ws(code, _ptr(llr), n_frames, L, algo,
+                                       C.byref(prune) if prune is not None else None, quant, _ptr(info_out),
+                                       _ptr(status_out), _ptr(pm_out), _ptr(workspace), workspace_bytes,
+                                       _stream(stream)))
+
+
+def pscl_encode(code, info, n_frames, x_out, stream=None):
+    return _check(lib().pscl_encode(code, _ptr(info), n_frames, _ptr(x_out), _stream(stream)))
+
+
+def pscl_debug_error_word() -> int:
+    w = C.c_uint32()
+    _check(lib().pscl_debug_error_word(C.byref(w)))
+    return w.value
+
+
+def pscl_debug_last_launches() -> int:
+    return lib().pscl_debug_last_launches()
+
+
+def pscl_set_tuning(target_warps_per_sm: int):
+    return _check(lib().pscl_set_tuning(int(target_warps_per_sm)))
+
+
+# ---------------------------------------------------------------------------
+class Code:
+    """Owning wrapper of a pscl_code with torch-allocated outputs."""
+
+    def __init__(self, frozen, crc_len=0, crc_poly=0, puncture=None, systematic=True):
+        import numpy as np
+        fr = np.asarray(frozen, dtype=np.uint8)
+        self.N = int(fr.size)
+        self.K = int(self.N - (fr != 0).sum())
+        self.crc_len = int(crc_len)
+        self.handle = pscl_create_code(self.N, self.K, fr, self.crc_len, int(crc_poly), puncture, int(systematic))
+        _, _, self.K_info, self.P = pscl_code_info(self.handle)
+        self.nbytes = (self.K_info + 7) // 8
+
+    def close(self):
+        if self.handle is not None:
+            pscl_destroy_code(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, llr, L, algo=PSCL_CASCL, prune=None, quant=PSCL_F32, want_pm=False, stream=None):
+        import torch
+        n = int(llr.shape[0])
+        dev = llr.device
+        info = torch.empty((n, self.nbytes), dtype=torch.uint8, device=dev)
+        status = torch.empty((n,), dtype=torch.int32, device=dev)
+        pm = torch.empty((n, L), dtype=torch.float32, device=dev) if want_pm else None
+        pscl_decode(self.handle, llr, n, L, algo, prune, quant, info, status, pm, stream)
+        return info, status, pm
+
+    def encode(self, info_packed, stream=None):
+        import torch
+        n = int(info_packed.shape[0])
+        x = torch.empty((n, self.N), dtype=torch.uint8, device=info_packed.device)
+        pscl_encode(self.handle, info_packed, n, x, stream)
+        return x

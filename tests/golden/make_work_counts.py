@@ -1,0 +1,42 @@
+"""Algorithmic work per frame of the benchmark workloads, counted by the oracle:
+f/g LLR updates summed over active paths, node steps, steps that discard
+candidates, and candidates offered.  The counts depend only on the code, the
+list size and the pruning (never on the data), so one frame suffices.
+Writes tests/golden/work_per_frame.json.  Run: python tests/golden/make_work_counts.py"""
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+CASES = [
+    ("c2_2048_1723", 32, None), ("c2_2048_1723", 32, "pruned"), ("c2_2048_1723", 1, None),
+    ("c2_2048_1723", 1, "pruned"), ("c1_cascl_128_64_L4", 4, None), ("c3_1024_512_L8", 8, None),
+    ("c3_1024_512_L8", 8, "pruned"),
+]
+
+
+def main():
+    out = {}
+    for name, L, pk in CASES:
+        d = synth.load_code(name)
+        code = oracle.Code(d["frozen"], d["crc_len"], d["crc_poly"], d["punct"], d["systematic"])
+        pr = oracle.pruning(15, rep_max=0, spc_max=4, r1_t=2, spc_t=4) if pk else None
+        st = oracle.Stats()
+        llr = np.full(code.N - code.P, 3.0)
+        oracle.decode(code, llr, L, oracle.CASCL, pr, oracle.F32, stats=st)
+        out[f"{name}_L{L}_{pk or 'unpruned'}"] = dict(
+            fg_elems=st.fg_elems, node_steps=st.node_steps, sorts=st.sorts, cand_total=st.cand_total,
+            N=code.N, K=code.K, K_info=code.K_info, L=L)
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "work_per_frame.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+        fh.write("\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,142 @@
+"""GPU decoder vs the oracle, element by element (decoded bits, status and
+every slot's path metric), on seeded BPSK-AWGN inputs.  Float results must be
+bit-exact: both sides apply the same operations in the same order, without
+fused multiply-adds."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import compare, describe, gpu_code, gpu_decode, make_inputs, oracle_decode
+
+pytestmark = pytest.mark.gpu
+
+PR_ALL = dict(mask=15, rep_max=0, spc_max=4, r1_t=2, spc_t=4)
+PR_I8 = dict(mask=15, rep_max=8, spc_max=4, r1_t=2, spc_t=4)
+
+
+def prunes(kind):
+    from paper_1710_08314_gb300 import pruning
+    if kind is None:
+        return None, None
+    p = PR_ALL if kind == "all" else PR_I8
+    return pruning(**p), oracle.pruning(**p)
+
+
+def run_case(name, n, ebn0, L, algo, quant, prune_kind, seed, systematic=True, frames=None):
+    d = synth.load_code(name)
+    code, info, llr = make_inputs(d, n, ebn0, seed, systematic)
+    gp, op = prunes(prune_kind)
+    gcode = gpu_code(d, systematic)
+    g = gpu_decode(gcode, llr, L, algo, quant, gp)
+    sub = llr if frames is None else llr[frames]
+    o = oracle_decode(code, sub, L, algo, quant, op)
+    bad = compare(g, o, frames)
+    assert not bad, f"{len(bad)} mismatching frames; first: " + describe(g, o, bad[0], frames)
+    return g, info
+
+
+def test_c1_plain_cascl_all_frames():
+    # (128, 64 incl. CRC-8), L = 4, float, no pruning, Eb/N0 = 2 dB, seed 1
+    run_case("c1_cascl_128_64_L4", 10000, 2.0, 4, "cascl", "f32", None, 1)
+
+
+@pytest.mark.parametrize("quant", ["f32", "i16", "i8"])
+@pytest.mark.parametrize("L", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("prune", [None, "all"])
+def test_small_codes_every_list_size(quant, L, prune):
+    pk = prune if not (prune and quant == "i8") else "i8"
+    run_case("c1_cascl_128_64_L4", 97, 1.5, L, "cascl", quant, pk, 10 + L)
+
+
+@pytest.mark.parametrize("name", ["u09", "u27", "u43", "u05", "mcs_128_40"])
+def test_punctured_and_mixed_rate_codes(name):
+    run_case(name, 150, 1.0, 8, "cascl", "f32", "all", 3)
+    run_case(name, 150, 1.0, 4, "cascl", "i8", "i8", 4)
+
+
+def test_non_systematic():
+    run_case("mcs_256_128", 120, 1.5, 8, "cascl", "f32", None, 5, systematic=False)
+    run_case("mcs_256_128", 120, 1.5, 8, "cascl", "i16", "all", 6, systematic=False)
+
+
+@pytest.mark.parametrize("algo", ["sc", "fascl", "pascl"])
+@pytest.mark.parametrize("quant", ["f32", "i8"])
+def test_adaptive_schedules(algo, quant):
+    run_case("mcs_256_128", 300, 1.0, 16, algo, quant, "all" if quant == "f32" else "i8", 7)
+
+
+def test_c3_pruned_int16_and_float():
+    run_case("c3_1024_512_L8", 64, 2.0, 8, "cascl", "i16", "all", 8)
+    run_case("c3_1024_512_L8", 64, 2.0, 8, "cascl", "f32", "all", 9)
+    run_case("c3_1024_512_L8", 16, 2.0, 8, "cascl", "f32", None, 10)
+
+
+def test_n2048_l32_sampled_frames():
+    # full-size launch: 2048 frames on the GPU, sampled frames on the oracle
+    frames = np.array([0, 1, 777, 2047])
+    run_case("c2_2048_1723", 2048, 3.5, 32, "cascl", "f32", None, 11, frames=frames)
+    run_case("c2_2048_1723", 2048, 3.5, 32, "fascl", "i8", "i8", 12, frames=frames)
+
+
+def test_tiny_codes_and_edge_shapes():
+    from paper_1710_08314_gb300 import pruning
+    rng = np.random.default_rng(0)
+    for N in [8, 16, 32, 64]:
+        for K in [1, N // 2, N - 1, N]:
+            fr = np.ones(N, dtype=np.uint8)
+            fr[rng.choice(N, K, replace=False)] = 0
+            crc = 8 if K > 8 else 0
+            d = dict(frozen=fr, crc_len=crc, crc_poly=synth.CRC_POLYS[crc], punct=None)
+            code = oracle.Code(fr, crc, synth.CRC_POLYS[crc], None, systematic=False)
+            llr = synth.random_llr(45, N, N + K)
+            gcode = gpu_code(d, systematic=False)
+            for L in [1, 4, 32]:
+                for quant in ["f32", "i8"]:
+                    for pk in [None, "all"]:
+                        gp, op = prunes(pk)
+                        g = gpu_decode(gcode, llr, L, "cascl", quant, gp)
+                        o = oracle_decode(code, llr, L, "cascl", quant, op)
+                        bad = compare(g, o)
+                        assert not bad, f"N={N} K={K} L={L} {quant} {pk}: " + describe(g, o, bad[0])
+
+
+def test_empty_and_ragged_batches():
+    d = synth.load_code("c1_cascl_128_64_L4")
+    gcode = gpu_code(d)
+    import torch
+    empty = torch.zeros((0, 128), dtype=torch.float32, device="cuda")
+    info, status, _ = gcode.decode(empty, 4)
+    assert info.shape[0] == 0
+    for n in [1, 7, 8, 9, 33]:
+        run_case("c1_cascl_128_64_L4", n, 2.0, 4, "cascl", "f32", None, 20 + n)
+
+
+def test_encoder_matches_oracle():
+    import torch
+    for name in ["c1_cascl_128_64_L4", "c2_2048_1723", "u09", "u43"]:
+        d = synth.load_code(name)
+        for systematic in [True, False]:
+            code = oracle.Code(d["frozen"], d["crc_len"], d["crc_poly"], d["punct"], systematic)
+            info = synth.info_bits(33, code.K_info, 3)
+            x = oracle.encode(code, info)
+            packed = np.packbits(info, axis=1)
+            g = gpu_code(d, systematic)
+            xg = g.encode(torch.from_numpy(packed).cuda()).cpu().numpy()
+            assert np.array_equal(xg, x), (name, systematic)
+
+
+def test_argument_errors():
+    from paper_1710_08314_gb300 import polarscl as ps
+    import torch
+    d = synth.load_code("c1_cascl_128_64_L4")
+    with pytest.raises(ps.PsclError):
+        ps.pscl_create_code(100, 50, np.zeros(100, np.uint8), 0, 0)
+    with pytest.raises(ps.PsclError):
+        ps.pscl_create_code(128, 65, d["frozen"], 8, 7)
+    g = gpu_code(d)
+    llr = torch.zeros((4, 128), device="cuda")
+    with pytest.raises(ps.PsclError):
+        g.decode(llr, 3)
+    with pytest.raises(ps.PsclError):
+        g.decode(llr, 4, prune=ps.pruning(15, r1_t=7))
