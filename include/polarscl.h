@@ -136,6 +136,25 @@ int pscl_decode_ws(pscl_code code, const float *llr, int n_frames, int L, pscl_a
                    int32_t *status_out, float *pm_out, void *workspace, size_t workspace_bytes,
                    void *stream);
 
+/* pscl_decode without any allocation, for callers that cannot allocate device
+ * memory while they decode (a real-time receive loop that must never
+ * synchronise the device, a process whose device memory belongs to another
+ * allocator, work that is set up once and afterwards only launched).  The
+ * paper has no counterpart; this is a deployment variant of pscl_decode.
+ * Same arguments and results as pscl_decode.  Scratch: a static device array
+ * of 32 MiB inside the library, held by every GPU that loads the library
+ * until the process exits and shared by all calls, so calls that overlap on
+ * the GPU race (serialise them on one stream).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  The node schedule must already exist:
+ * call pscl_prepare(code, pruning) at set-up (it allocates there).
+ * Errors: PSCL_EINVAL when the schedule is not prepared or when one block's
+ * per-warp scratch plus the adaptive frame lists (8 bytes per frame) exceed
+ * 32 MiB; otherwise as pscl_decode.                                         */
+int pscl_decode_static(pscl_code code, const float *llr, int n_frames, int L, pscl_algo algo,
+                       const pscl_pruning *pruning, pscl_quant quant, uint8_t *info_out,
+                       int32_t *status_out, float *pm_out, void *stream);
+
 /* Encode n_frames frames (Sec. II-A): info: device, n_frames x
  * ceil(K_info/8) bytes packed MSB first; x_out: device, n_frames x N bytes,
  * one codeword bit (0/1) per byte, punctured positions included.           */

@@ -301,6 +301,20 @@ static int get_program(pscl_code c, const pscl_pruning *pr, Program *out)
     return PSCL_OK;
 }
 
+// lookup of an already prepared schedule; never builds or allocates
+static int find_program(pscl_code c, const pscl_pruning *pr, Program *out)
+{
+    int rc = check_pruning(pr);
+    if (rc) return rc;
+    std::vector<int> key = prune_key(pr);
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->programs.find(key);
+    if (it == c->programs.end())
+        return fail(PSCL_EINVAL, "no node schedule for this pruning setting: call pscl_prepare first");
+    *out = it->second;
+    return PSCL_OK;
+}
+
 extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
@@ -392,7 +406,7 @@ static const int kWarpsPerBlock = 4;
 static int g_target_warps_per_sm = 8;
 
 static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const pscl_pruning *pr, pscl_quant quant,
-                     Plan *pl)
+                     Plan *pl, bool build_program = true)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
     if (n_frames < 0) return fail(PSCL_EINVAL, "n_frames=%d", n_frames);
@@ -403,7 +417,7 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     int dev;
     CU(cudaGetDevice(&dev));
     if (dev != c->dev) return fail(PSCL_EINVAL, "code was created on device %d, current device is %d", c->dev, dev);
-    int rc = get_program(c, pr, &pl->pg);
+    int rc = build_program ? get_program(c, pr, &pl->pg) : find_program(c, pr, &pl->pg);
     if (rc) return rc;
     DevProps dp;
     rc = get_props(&dp);
@@ -633,4 +647,71 @@ extern "C" int pscl_debug_checked(void)
 #else
     return 0;
 #endif
+}
+
+// ---------------------------------------------------------------------------
+// Decoding without any allocation.
+//
+// Some callers cannot allocate device memory at decode time: code running
+// where cudaMalloc is forbidden or would stall (a real-time receive loop that
+// must not synchronise the device, a host process whose memory is handed out
+// by another allocator, or work that is set up once and then only launched).
+// pscl_decode_static serves them: its scratch is the file-scope device array
+// below, of PSCL_STATIC_SCRATCH_BYTES bytes, which every GPU that loads this
+// library holds until the process exits.  Its device address is looked up
+// once per device with cudaGetSymbolAddress (a host-side name of the array is
+// not a device address).
+#define PSCL_STATIC_SCRATCH_BYTES (32u << 20)
+static __device__ __align__(256) unsigned char g_static_scratch[PSCL_STATIC_SCRATCH_BYTES];
+static std::map<int, void *> g_static_ptr;
+
+static int static_scratch(void **out)
+{
+    int dev;
+    CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_static_ptr.find(dev);
+    if (it == g_static_ptr.end()) {
+        void *ptr = nullptr;
+        CU(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        it = g_static_ptr.emplace(dev, ptr).first;
+    }
+    *out = it->second;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_decode_static(pscl_code c, const float *llr, int n_frames, int L, pscl_algo algo,
+                                  const pscl_pruning *pr, pscl_quant quant, uint8_t *info_out,
+                                  int32_t *status_out, float *pm_out, void *stream)
+{
+    Plan pl;
+    int rc = make_plan(c, n_frames, L, algo, pr, quant, &pl, false);
+    if (rc) return rc;
+    void *ws;
+    rc = static_scratch(&ws);
+    if (rc) return rc;
+    // fit the resident warps to the array: frames beyond them are handled by
+    // the kernel's task loop, so only the per-warp slice and the adaptive
+    // frame lists bound what can be decoded
+    const size_t fixed = 256 + pl.list_bytes;
+    const size_t per_warp = pl.total_warps ? pl.gmem_scratch / (size_t)pl.total_warps : 0;
+    if (fixed + (size_t)kWarpsPerBlock * per_warp > PSCL_STATIC_SCRATCH_BYTES)
+        return fail(PSCL_EINVAL,
+                    "pscl_decode_static: needs %zu bytes of scratch (%zu for frame lists, %zu per warp x %d) "
+                    "but its static scratch holds %u bytes",
+                    fixed + (size_t)kWarpsPerBlock * per_warp, pl.list_bytes, per_warp, kWarpsPerBlock,
+                    PSCL_STATIC_SCRATCH_BYTES);
+    if (per_warp > 0) {
+        size_t fit = (PSCL_STATIC_SCRATCH_BYTES - fixed) / per_warp;
+        if (fit < (size_t)pl.total_warps) {
+            pl.total_warps = (int)(fit / kWarpsPerBlock) * kWarpsPerBlock;
+            pl.grid = pl.total_warps / kWarpsPerBlock;
+            pl.gmem_scratch = per_warp * (size_t)pl.total_warps;
+            pl.total_ws = fixed + pl.gmem_scratch;
+        }
+    }
+    // the debug word and the list counters start at zero on every call
+    CU(cudaMemsetAsync(ws, 0, 256, (cudaStream_t)stream));
+    return run_decode(c, llr, n_frames, L, algo, pr, quant, info_out, status_out, pm_out, ws,
+                      PSCL_STATIC_SCRATCH_BYTES, (cudaStream_t)stream, pl);
 }

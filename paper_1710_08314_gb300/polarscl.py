@@ -60,6 +60,7 @@ def lib() -> C.CDLL:
             L.pscl_workspace_size.argtypes = [vp, i, i, i, vp, i, C.POINTER(C.c_size_t)]
             L.pscl_decode_ws.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp, C.c_size_t, vp]
             L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
+            L.pscl_decode_static.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
             L.pscl_last_error.restype = C.c_char_p
             L.pscl_version.restype = C.c_char_p
             L.pscl_debug_error_word.argtypes = [C.POINTER(u32)]
@@ -144,6 +145,14 @@ def pscl_decode_ws(code, llr, n_frames, L, algo, prune, quant, info_out, status_
                                        C.byref(prune) if prune is not None else None, quant, _ptr(info_out),
                                        _ptr(status_out), _ptr(pm_out), _ptr(workspace), workspace_bytes,
                                        _stream(stream)))
+
+
+def pscl_decode_static(code, llr, n_frames, L, algo, prune, quant, info_out, status_out, pm_out=None,
+                       stream=None):
+    """pscl_decode with the library's static scratch: allocates nothing."""
+    return _check(lib().pscl_decode_static(code, _ptr(llr), n_frames, L, algo,
+                                           C.byref(prune) if prune is not None else None, quant,
+                                           _ptr(info_out), _ptr(status_out), _ptr(pm_out), _stream(stream)))
 
 
 def pscl_encode(code, info, n_frames, x_out, stream=None):
