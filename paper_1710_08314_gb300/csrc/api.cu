@@ -241,6 +241,13 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int 
         if (d > max_depth) max_depth = d;
         return PSCL_OK;
     }
+    if (S == 2) {
+        // both children are leaves: one fused step, which reads layer d only
+        ops.push_back(op_make(OP_PAIR, (uint32_t)d, (uint32_t)(c->frozen[o] | (c->frozen[o + 1] << 1)),
+                              (uint32_t)side, 0));
+        if (d > max_depth) max_depth = d;
+        return PSCL_OK;
+    }
     ops.push_back(op_make(OP_F, (uint32_t)d, 0, 0, 0));
     int rc = gen_program(c, pr, d + 1, o, S / 2, 0, ops, max_depth);
     if (rc) return rc;

@@ -19,6 +19,8 @@ enum Opcode : uint32_t {
     OP_G = 1,     // layer d+1 = g(layer d, beta_left)     (right child LLRs)
     OP_NODE = 2,  // leaf or pruned node at depth d
     OP_COMB = 3,  // right child at depth d done: parent beta = h(left, right)
+    OP_PAIR = 4,  // size-2 node at depth d with two leaf children, fused
+                  //   (type bit 0: left leaf frozen, bit 1: right leaf frozen)
 };
 enum NodeType : uint32_t { NT_R0 = 1, NT_R1 = 2, NT_REP = 3, NT_SPC = 4 };
 

@@ -54,6 +54,8 @@ struct QF32 {
     __device__ static __forceinline__ uint32_t quant(float x) { return __float_as_uint(x); }
     __device__ static __forceinline__ float to_float(V v) { return v; }
     __device__ static __forceinline__ V sub(V a, V) { return a; }
+    __device__ static __forceinline__ V f1(V a, V b) { return __uint_as_float(F(__float_as_uint(a), __float_as_uint(b))); }
+    __device__ static __forceinline__ V g1(V a, V b, uint32_t s) { return __fadd_rn(s ? -a : a, b); }
 };
 
 struct QI16 {
@@ -86,6 +88,16 @@ struct QI16 {
     }
     __device__ static __forceinline__ float to_float(V v) { return (float)v; }
     __device__ static __forceinline__ V sub(V a, V b) { return a - b; }
+    __device__ static __forceinline__ V f1(V a, V b)
+    {
+        const V m = min(a < 0 ? -a : a, b < 0 ? -b : b);
+        return ((a < 0) != (b < 0)) ? -m : m;
+    }
+    __device__ static __forceinline__ V g1(V a, V b, uint32_t s)
+    {
+        const V x = (s ? -a : a) + b;
+        return x > Q ? Q : (x < -Q ? -Q : x);
+    }
 };
 
 struct QI8 {
@@ -118,6 +130,16 @@ struct QI8 {
     }
     __device__ static __forceinline__ float to_float(V v) { return (float)v; }
     __device__ static __forceinline__ V sub(V a, V b) { return a - b; }
+    __device__ static __forceinline__ V f1(V a, V b)
+    {
+        const V m = min(a < 0 ? -a : a, b < 0 ? -b : b);
+        return ((a < 0) != (b < 0)) ? -m : m;
+    }
+    __device__ static __forceinline__ V g1(V a, V b, uint32_t s)
+    {
+        const V x = (s ? -a : a) + b;
+        return x > Q ? Q : (x < -Q ? -Q : x);
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -445,6 +467,98 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
     newkey = e1;
 }
 
+// Two candidates per path (an information leaf, or a REP node): candidate
+// (p, 0) has metric key ka, (p, 1) key kb, candidate ids c = 2p and 2p + 1.
+// Same result as select_paths<2>: the L smallest (PM, c) survive and take new
+// slots in increasing c.  When every path's second candidate ranks after
+// every first candidate, the first candidates are the survivors and no sort
+// is needed; otherwise the L-th smallest metric value is found with a 32-bit
+// bitonic network and ties at that value are resolved in candidate order.
+__device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int &par, int &cand,
+                                          uint32_t &newkey, int &n_keep)
+{
+    const int na = c.n_active, L = c.L;
+    if (2 * na <= L) {
+        n_keep = 2 * na;
+        const bool live = c.slot < n_keep;
+        par = live ? c.slot >> 1 : 0;
+        cand = live ? c.slot & 1 : 0;
+        const uint32_t x0 = __shfl_sync(PSCL_FULL, ka, c.seg + par);
+        const uint32_t x1 = __shfl_sync(PSCL_FULL, kb, c.seg + par);
+        newkey = cand ? x1 : x0;
+        return;
+    }
+    n_keep = L;
+    const bool act = c.slot < na;
+    const uint32_t a = act ? ka : 0xFFFFFFFFu, b = act ? kb : 0xFFFFFFFFu;
+    if (na == L) {
+        uint32_t mx = a, mn = b;
+        for (int m = 1; m < L; m <<= 1) {
+            mx = max(mx, __shfl_xor_sync(PSCL_FULL, mx, m));
+            mn = min(mn, __shfl_xor_sync(PSCL_FULL, mn, m));
+        }
+        // every frame of the warp must agree: the shuffles below are warp-wide
+        if (__all_sync(PSCL_FULL, mn > mx)) {
+            par = c.slot;
+            cand = 0;
+            newkey = ka;
+            return;
+        }
+    }
+    // L-th smallest metric value: bitonic sort of 2L values, element e = 2*slot + m
+    uint32_t k0 = a, k1 = b;
+    for (int size = 2; size <= 2 * L; size <<= 1) {
+        const bool up = ((c.slot << 1) & size) == 0;
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 1) {
+                const uint32_t lo = min(k0, k1), hi = max(k0, k1);
+                k0 = up ? lo : hi;
+                k1 = up ? hi : lo;
+            } else {
+                const int ls = stride >> 1;
+                const bool takemin = ((c.slot & ls) == 0) == up;
+                const uint32_t o0 = __shfl_xor_sync(PSCL_FULL, k0, ls);
+                const uint32_t o1 = __shfl_xor_sync(PSCL_FULL, k1, ls);
+                k0 = takemin ? min(k0, o0) : max(k0, o0);
+                k1 = takemin ? min(k1, o1) : max(k1, o1);
+            }
+        }
+    }
+    const int tp = (L - 1) >> 1;
+    const uint32_t tsel = ((L - 1) & 1) ? k1 : k0;
+    const uint32_t tau = __shfl_sync(PSCL_FULL, tsel, c.seg + tp);
+    const uint32_t segmask = L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << c.seg);
+    const uint32_t lt = ((1u << c.lane) - 1u) & segmask;
+    const uint32_t BA = __ballot_sync(PSCL_FULL, a < tau) & segmask;
+    const uint32_t BB = __ballot_sync(PSCL_FULL, b < tau) & segmask;
+    const uint32_t EA = __ballot_sync(PSCL_FULL, a == tau) & segmask;
+    const uint32_t EB = __ballot_sync(PSCL_FULL, b == tau) & segmask;
+    const int need = L - __popc(BA) - __popc(BB);
+    const int ra = __popc(EA & lt) + __popc(EB & lt);
+    const bool sa = a < tau || (a == tau && ra < need);
+    const int rb = ra + (a == tau ? 1 : 0);
+    const bool sb = b < tau || (b == tau && rb < need);
+    const uint32_t SA = __ballot_sync(PSCL_FULL, sa) & segmask;
+    const uint32_t SB = __ballot_sync(PSCL_FULL, sb) & segmask;
+    int r = __popc(SA & lt) + __popc(SB & lt);
+    uint32_t *src = (uint32_t *)(c.sm + c.P->lay.src_off);
+    if (sa) {
+        src[2 * (c.seg + r)] = (uint32_t)c.slot << 8;
+        src[2 * (c.seg + r) + 1] = ka;
+        ++r;
+    }
+    if (sb) {
+        src[2 * (c.seg + r)] = ((uint32_t)c.slot << 8) | 1u;
+        src[2 * (c.seg + r) + 1] = kb;
+    }
+    __syncwarp();
+    const uint32_t e0 = src[2 * c.lane], e1 = src[2 * c.lane + 1];
+    __syncwarp();
+    par = (int)(e0 >> 8) & (L - 1);
+    cand = (int)(e0 & 1u);
+    newkey = e1;
+}
+
 // ---------------------------------------------------------------------------
 // A leaf or pruned node at depth d (Sec. II-B; candidate rules as in the
 // header notes of the oracle and the ABI).
@@ -458,7 +572,8 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
     const uint32_t capd = c.P->lay.b_words[d];
     int par, cand, n_keep;
     uint32_t newkey;
-    select_paths<M>(c, kp, par, cand, newkey, n_keep);
+    if constexpr (M == 2) select_m2(c, kp[0], kp[1], par, cand, newkey, n_keep);
+    else select_paths<M>(c, kp, par, cand, newkey, n_keep);
     const int pl = c.seg + par;
     // the new path inherits its parent's slot tables (lazy copy)
     c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
@@ -507,7 +622,7 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
 }
 
 template <class Qt>
-__device__ __noinline__ void op_node(Ctx &c, int d, int type, int side, int t, typename Qt::V &pm)
+__device__ __forceinline__ void op_node(Ctx &c, int d, int type, int side, int t, typename Qt::V &pm)
 {
     typedef typename Qt::V V;
     const int S = c.N >> d;
@@ -623,6 +738,74 @@ __device__ __noinline__ void op_node(Ctx &c, int d, int type, int side, int t, t
     default: PSCL_CANDS(16) break;
     }
 #undef PSCL_CANDS
+}
+
+// A size-2 node whose children are leaves, in registers: f, left leaf, g,
+// right leaf and h of Algorithm 1 in one step.  lfz / rfz: the left / right
+// leaf is frozen.  After a selection the new path takes its parent's two node
+// LLRs and left decision by shuffle (its lazy copy of this node).
+template <class Qt>
+__device__ __forceinline__ void op_pair(Ctx &c, int d, int side, int lfz, int rfz, typename Qt::V &pm)
+{
+    typedef typename Qt::V V;
+    const uint32_t *in = llr_layer(c, d);
+    const uint32_t cap = c.P->lay.llr_words[d];
+    const int cin = c.seg + tab_get(c.idxL, d);
+    V a0, a1;
+    if (Qt::EPW == 1) {
+        a0 = Qt::elem(ld(c, in, cin, cap, 1u), 0);
+        a1 = Qt::elem(ld(c, in, 32 + cin, cap, 1u), 0);
+    } else {
+        const uint32_t w = ld(c, in, cin, cap, 1u);
+        a0 = Qt::elem(w, 0);
+        a1 = Qt::elem(w, 1);
+    }
+    // left leaf: LLR f(a0, a1)
+    V lam = Qt::f1(a0, a1);
+    uint32_t uL = 0;
+    if (lfz) {
+        pm = Qt::add(pm, lam < 0 ? Qt::absv(lam) : Qt::zero());
+    } else {
+        int par, cand, nk;
+        uint32_t nkey;
+        select_m2(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk);
+        const int pl = c.seg + par;
+        c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
+        c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
+        c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
+        c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
+        a0 = __shfl_sync(PSCL_FULL, a0, pl);
+        a1 = __shfl_sync(PSCL_FULL, a1, pl);
+        const uint32_t hd = __shfl_sync(PSCL_FULL, (uint32_t)(lam < 0), pl);
+        uL = hd ^ (uint32_t)cand;
+        pm = Qt::from_key(nkey);
+        c.n_active = nk;
+    }
+    normalise<Qt>(c, pm);
+    // right leaf: LLR g(a0, a1, uL)
+    lam = Qt::g1(a0, a1, uL);
+    uint32_t uR = 0;
+    if (rfz) {
+        pm = Qt::add(pm, lam < 0 ? Qt::absv(lam) : Qt::zero());
+    } else {
+        int par, cand, nk;
+        uint32_t nkey;
+        select_m2(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk);
+        const int pl = c.seg + par;
+        c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
+        c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
+        c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
+        c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
+        uL = __shfl_sync(PSCL_FULL, uL, pl);
+        const uint32_t hd = __shfl_sync(PSCL_FULL, (uint32_t)(lam < 0), pl);
+        uR = hd ^ (uint32_t)cand;
+        pm = Qt::from_key(nkey);
+        c.n_active = nk;
+    }
+    normalise<Qt>(c, pm);
+    uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
+    st(c, dst, c.lane, c.P->lay.b_words[d], (uL ^ uR) | (uR << 1), 64u);
+    if (side == 0) tab_set(c.idxS, d, c.slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -762,6 +945,7 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         case OP_F: op_f<Qt>(c, d); break;
         case OP_G: op_g<Qt>(c, d); break;
         case OP_COMB: op_comb(c, d, op_side(op)); break;
+        case OP_PAIR: op_pair<Qt>(c, d, op_side(op), (int)(op_type(op) & 1u), (int)((op_type(op) >> 1) & 1u), pm); break;
         default: op_node<Qt>(c, d, (int)op_type(op), op_side(op), op_t(op), pm); break;
         }
         __syncwarp();
