@@ -72,8 +72,8 @@ typedef enum { PSCL_F32 = 0, PSCL_I16 = 1, PSCL_I8 = 2 } pscl_quant;
  * rep_max: 0 = no limit (REP2+), 8 = REP8-.  spc_max: 4 = SPC4 (size 4
  * only), 0 = no limit (SPC4+).  r1_max: 0 = no limit.  r1_t / spc_t: how many
  * least-reliable positions the R1 / SPC candidates flip (r1_t = 2 is the
- * paper's Chase-2, Sec. IV-B); the kernels accept 1 <= r1_t <= 4 and
- * 1 <= spc_t <= 5.  mask = 0 decodes the full tree leaf by leaf.            */
+ * paper's Chase-2, Sec. IV-B); the kernels accept 1 <= r1_t <= 3 and
+ * 1 <= spc_t <= 4.  mask = 0 decodes the full tree leaf by leaf.            */
 typedef struct {
     uint32_t mask;
     int rep_max;

@@ -223,6 +223,17 @@ static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
     return 0;
 }
 
+// largest subtree decoded in registers (2, 4 or 8 leaves; 1 = none)
+static int g_fuse_max = 8;
+
+// true when no node of the subtree of S leaves at o is a pruned node
+static bool subtree_unpruned(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
+{
+    if (S == 1) return true;
+    if (classify(c, pr, o, S)) return false;
+    return subtree_unpruned(c, pr, o, S / 2) && subtree_unpruned(c, pr, o + S / 2, S / 2);
+}
+
 static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int o, int S, int side,
                        std::vector<uint32_t> &ops, int &max_depth)
 {
@@ -232,19 +243,20 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int 
         if (type == NT_R1) {
             int r1t = pr ? pr->r1_t : 1;
             t = S == 1 ? 1 : (r1t < S ? r1t : S);
-            if (t < 1 || t > 4) return fail(PSCL_EUNSUPPORTED, "R1 flip depth %d (node size %d) outside 1..4", t, S);
+            if (t < 1 || t > 3) return fail(PSCL_EUNSUPPORTED, "R1 flip depth %d (node size %d) outside 1..3", t, S);
         } else if (type == NT_SPC) {
             t = pr->spc_t < S ? pr->spc_t : S;
-            if (t < 1 || t > 5) return fail(PSCL_EUNSUPPORTED, "SPC flip depth %d (node size %d) outside 1..5", t, S);
+            if (t < 1 || t > 4) return fail(PSCL_EUNSUPPORTED, "SPC flip depth %d (node size %d) outside 1..4", t, S);
         }
         ops.push_back(op_make(OP_NODE, (uint32_t)d, (uint32_t)type, (uint32_t)side, (uint32_t)t));
         if (d > max_depth) max_depth = d;
         return PSCL_OK;
     }
-    if (S == 2) {
-        // both children are leaves: one fused step, which reads layer d only
-        ops.push_back(op_make(OP_PAIR, (uint32_t)d, (uint32_t)(c->frozen[o] | (c->frozen[o + 1] << 1)),
-                              (uint32_t)side, 0));
+    if (d >= 1 && S <= g_fuse_max && subtree_unpruned(c, pr, o, S)) {
+        // the whole subtree is decoded in registers by one step
+        uint32_t fz = 0;
+        for (int i = 0; i < S; i++) fz |= (uint32_t)c->frozen[o + i] << i;
+        ops.push_back(op_make(OP_RSUB, (uint32_t)d, 0, (uint32_t)side, 0) | (fz << 16));
         if (d > max_depth) max_depth = d;
         return PSCL_OK;
     }
@@ -260,8 +272,8 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int 
 
 static std::vector<int> prune_key(const pscl_pruning *pr)
 {
-    if (!pr || pr->mask == 0) return {0};
-    return {(int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
+    if (!pr || pr->mask == 0) return {g_fuse_max, 0};
+    return {g_fuse_max, (int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
 }
 
 static int check_pruning(const pscl_pruning *pr)
@@ -270,10 +282,10 @@ static int check_pruning(const pscl_pruning *pr)
     if (pr->mask & ~15u) return fail(PSCL_EINVAL, "pruning mask 0x%x has unknown bits", pr->mask);
     if (pr->rep_max < 0 || pr->spc_max < 0 || pr->r1_max < 0)
         return fail(PSCL_EINVAL, "negative pruning size limit");
-    if ((pr->mask & PSCL_PRUNE_R1) && (pr->r1_t < 1 || pr->r1_t > 4))
-        return fail(PSCL_EUNSUPPORTED, "r1_t=%d: the kernels support 1..4", pr->r1_t);
-    if ((pr->mask & PSCL_PRUNE_SPC) && (pr->spc_t < 1 || pr->spc_t > 5))
-        return fail(PSCL_EUNSUPPORTED, "spc_t=%d: the kernels support 1..5", pr->spc_t);
+    if ((pr->mask & PSCL_PRUNE_R1) && (pr->r1_t < 1 || pr->r1_t > 3))
+        return fail(PSCL_EUNSUPPORTED, "r1_t=%d: the kernels support 1..3", pr->r1_t);
+    if ((pr->mask & PSCL_PRUNE_SPC) && (pr->spc_t < 1 || pr->spc_t > 4))
+        return fail(PSCL_EUNSUPPORTED, "spc_t=%d: the kernels support 1..4", pr->spc_t);
     return PSCL_OK;
 }
 
@@ -347,7 +359,8 @@ static void make_layout(const pscl_code_s *c, const Program &pg, int L, int quan
     for (int d = maxd; d >= 0; d--) {
         const int S = c->N >> d;
         const uint32_t rows = (uint32_t)((S + EPW - 1) / EPW);
-        const uint32_t words = rows * (uint32_t)(d == 0 ? fpw : 32);
+        // words of a path are stored in groups of four (16-byte accesses)
+        const uint32_t words = ((rows + 3u) / 4u) * 4u * (uint32_t)(d == 0 ? fpw : 32);
         const uint32_t bwords = (uint32_t)(S >= 32 ? S / 32 : 1) * 32u;
         // LLR layer d
         lay->llr_words[d] = words;
@@ -410,7 +423,7 @@ struct Plan {
 
 static const int kWarpsPerBlock = 4;
 // target resident warps per SM; each warp's shared slice is sized to fit
-static int g_target_warps_per_sm = 8;
+static int g_target_warps_per_sm = 16;
 
 static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const pscl_pruning *pr, pscl_quant quant,
                      Plan *pl, bool build_program = true)
@@ -644,6 +657,14 @@ extern "C" int pscl_set_tuning(int target_warps_per_sm)
 {
     if (target_warps_per_sm < 1 || target_warps_per_sm > 64) return fail(PSCL_EINVAL, "target warps per SM out of range");
     g_target_warps_per_sm = target_warps_per_sm;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_set_fusion(int max_leaves)
+{
+    if (max_leaves != 1 && max_leaves != 2 && max_leaves != 4 && max_leaves != 8)
+        return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8", max_leaves);
+    g_fuse_max = max_leaves;
     return PSCL_OK;
 }
 

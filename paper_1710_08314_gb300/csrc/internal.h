@@ -13,14 +13,14 @@ constexpr int kMaxLayers = kMaxLog2N + 1;
 // pre-order traversal of Algorithm 1, with pruned nodes as single steps).
 //   bits 0..3  opcode      bits 4..7  depth d      bits 8..10 node type
 //   bit  11    side (0 = left child, 1 = right child or root)
-//   bits 12..15 flip depth t
+//   bits 12..15 flip depth t   (OP_RSUB: bits 16..31 frozen-leaf mask)
 enum Opcode : uint32_t {
     OP_F = 0,     // layer d+1 = f(layer d)               (left child LLRs)
     OP_G = 1,     // layer d+1 = g(layer d, beta_left)     (right child LLRs)
     OP_NODE = 2,  // leaf or pruned node at depth d
     OP_COMB = 3,  // right child at depth d done: parent beta = h(left, right)
-    OP_PAIR = 4,  // size-2 node at depth d with two leaf children, fused
-                  //   (type bit 0: left leaf frozen, bit 1: right leaf frozen)
+    OP_RSUB = 4,  // unpruned subtree of 2..8 leaves at depth d, decoded in
+                  //   registers; bits 16..31: frozen mask of its leaves
 };
 enum NodeType : uint32_t { NT_R0 = 1, NT_R1 = 2, NT_REP = 3, NT_SPC = 4 };
 

@@ -203,6 +203,11 @@ __device__ __forceinline__ uint32_t *br_layer(const Ctx &c, int d)
     return (uint32_t *)(b + c.P->lay.br_off[d]);
 }
 
+// LLR layers store the words of a path in groups of four: word w of column
+// col sits at ((w / 4) * width + col) * 4 + w % 4, so a lane moves four
+// consecutive words with one 16-byte access and a warp row is 512 bytes.
+__device__ __forceinline__ int qa(int w, int col, int width) { return (((w >> 2) * width + col) << 2) + (w & 3); }
+
 __device__ __forceinline__ uint32_t ld(const Ctx &c, const uint32_t *p, int idx, uint32_t cap, uint32_t code)
 {
     if (!PSCL_OK_IDX(c, idx, cap, code)) return 0u;
@@ -212,6 +217,20 @@ __device__ __forceinline__ void st(const Ctx &c, uint32_t *p, int idx, uint32_t 
 {
     if (!PSCL_OK_IDX(c, idx, cap, code)) return;
     p[idx] = v;
+}
+// quad q of column col (16-byte aligned)
+__device__ __forceinline__ uint4 ld4(const Ctx &c, const uint32_t *p, int q, int col, int width, uint32_t cap,
+                                     uint32_t code)
+{
+    const int idx = (q * width + col) << 2;
+    if (!PSCL_OK_IDX(c, idx + 3, cap, code)) return make_uint4(0u, 0u, 0u, 0u);
+    return *reinterpret_cast<const uint4 *>(p + idx);
+}
+__device__ __forceinline__ void st4(const Ctx &c, uint32_t *p, int q, int col, uint32_t cap, uint4 v, uint32_t code)
+{
+    const int idx = (q * 32 + col) << 2;
+    if (!PSCL_OK_IDX(c, idx + 3, cap, code)) return;
+    *reinterpret_cast<uint4 *>(p + idx) = v;
 }
 
 __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src)
@@ -229,6 +248,8 @@ __device__ __forceinline__ uint64_t shfl64_xor(uint64_t v, int m)
 
 // ---------------------------------------------------------------------------
 // f step at depth d: layer d+1 (own column) = f(layer d) for the left child.
+// Slots without an active path skip the memory traffic (their columns are
+// never read before being rewritten).
 template <class Qt>
 __device__ __forceinline__ void op_f(Ctx &c, int d)
 {
@@ -238,17 +259,28 @@ __device__ __forceinline__ void op_f(Ctx &c, int d)
     const uint32_t cap_in = c.P->lay.llr_words[d], cap_out = c.P->lay.llr_words[d + 1];
     const int win = d == 0 ? c.fpw : 32;
     const int cin = d == 0 ? c.fiw : c.seg + tab_get(c.idxL, d);
-    if (H >= Qt::EPW) {
-        const int HW = H / Qt::EPW;
-#pragma unroll 4
-        for (int w = 0; w < HW; ++w) {
-            uint32_t a = ld(c, in, w * win + cin, cap_in, 1u);
-            uint32_t b = ld(c, in, (w + HW) * win + cin, cap_in, 1u);
-            st(c, out, w * 32 + c.lane, cap_out, Qt::F(a, b), 2u);
+    const bool act = c.slot < c.n_active;
+    if (act) {
+        if (H >= 4 * Qt::EPW) {
+            const int HQ = H / (4 * Qt::EPW);
+#pragma unroll 2
+            for (int q = 0; q < HQ; ++q) {
+                const uint4 a = ld4(c, in, q, cin, win, cap_in, 1u);
+                const uint4 b = ld4(c, in, q + HQ, cin, win, cap_in, 1u);
+                st4(c, out, q, c.lane, cap_out,
+                    make_uint4(Qt::F(a.x, b.x), Qt::F(a.y, b.y), Qt::F(a.z, b.z), Qt::F(a.w, b.w)), 2u);
+            }
+        } else if (H >= Qt::EPW) {
+            const int HW = H / Qt::EPW;
+            for (int w = 0; w < HW; ++w) {
+                const uint32_t a = ld(c, in, qa(w, cin, win), cap_in, 1u);
+                const uint32_t b = ld(c, in, qa(w + HW, cin, win), cap_in, 1u);
+                st(c, out, qa(w, c.lane, 32), cap_out, Qt::F(a, b), 2u);
+            }
+        } else {
+            const uint32_t wd = ld(c, in, qa(0, cin, win), cap_in, 1u);
+            st(c, out, qa(0, c.lane, 32), cap_out, Qt::F(wd, wd >> (H * Qt::BITS)), 2u);
         }
-    } else {
-        uint32_t wd = ld(c, in, cin, cap_in, 1u);
-        st(c, out, c.lane, cap_out, Qt::F(wd, wd >> (H * Qt::BITS)), 2u);
     }
     tab_set(c.idxL, d + 1, c.slot);
 }
@@ -267,25 +299,41 @@ __device__ __forceinline__ void op_g(Ctx &c, int d)
     const int win = d == 0 ? c.fpw : 32;
     const int cin = d == 0 ? c.fiw : c.seg + tab_get(c.idxL, d);
     const int cs = c.seg + tab_get(c.idxS, d + 1);
-    if (H >= Qt::EPW) {
-        const int HW = H / Qt::EPW;
-        constexpr int WPB = 32 / Qt::EPW;  // LLR words per 32-bit beta word
-        for (int w0 = 0; w0 < HW; w0 += WPB) {
-            uint32_t bw = ld(c, bl, (w0 / WPB) * 32 + cs, cap_b, 4u);
-            const int cnt = HW - w0 < WPB ? HW - w0 : WPB;
-#pragma unroll 4
-            for (int k = 0; k < cnt; ++k) {
-                const int w = w0 + k;
-                uint32_t a = ld(c, in, w * win + cin, cap_in, 1u);
-                uint32_t b = ld(c, in, (w + HW) * win + cin, cap_in, 1u);
-                uint32_t s = (bw >> (k * Qt::EPW)) & ((1u << Qt::EPW) - 1u);
-                st(c, out, w * 32 + c.lane, cap_out, Qt::G(a, b, s), 2u);
+    const bool act = c.slot < c.n_active;
+    constexpr uint32_t M1 = (1u << Qt::EPW) - 1u;
+    if (act) {
+        if (H >= 4 * Qt::EPW) {
+            const int HQ = H / (4 * Qt::EPW);
+            constexpr int QPB = 32 / (4 * Qt::EPW);  // quads per 32-bit beta word
+            for (int q0 = 0; q0 < HQ; q0 += QPB) {
+                const uint32_t bw = ld(c, bl, (q0 / QPB) * 32 + cs, cap_b, 4u);
+                const int cnt = HQ - q0 < QPB ? HQ - q0 : QPB;
+#pragma unroll 2
+                for (int k = 0; k < cnt; ++k) {
+                    const int q = q0 + k;
+                    const uint4 a = ld4(c, in, q, cin, win, cap_in, 1u);
+                    const uint4 b = ld4(c, in, q + HQ, cin, win, cap_in, 1u);
+                    const uint32_t sb = bw >> (k * 4 * Qt::EPW);
+                    st4(c, out, q, c.lane, cap_out,
+                        make_uint4(Qt::G(a.x, b.x, sb & M1), Qt::G(a.y, b.y, (sb >> Qt::EPW) & M1),
+                                   Qt::G(a.z, b.z, (sb >> (2 * Qt::EPW)) & M1),
+                                   Qt::G(a.w, b.w, (sb >> (3 * Qt::EPW)) & M1)),
+                        2u);
+                }
             }
+        } else if (H >= Qt::EPW) {
+            const int HW = H / Qt::EPW;
+            const uint32_t bw = ld(c, bl, cs, cap_b, 4u);
+            for (int w = 0; w < HW; ++w) {
+                const uint32_t a = ld(c, in, qa(w, cin, win), cap_in, 1u);
+                const uint32_t b = ld(c, in, qa(w + HW, cin, win), cap_in, 1u);
+                st(c, out, qa(w, c.lane, 32), cap_out, Qt::G(a, b, (bw >> (w * Qt::EPW)) & M1), 2u);
+            }
+        } else {
+            const uint32_t wd = ld(c, in, qa(0, cin, win), cap_in, 1u);
+            const uint32_t sb = ld(c, bl, cs, cap_b, 4u) & ((1u << H) - 1u);
+            st(c, out, qa(0, c.lane, 32), cap_out, Qt::G(wd, wd >> (H * Qt::BITS), sb), 2u);
         }
-    } else {
-        uint32_t wd = ld(c, in, cin, cap_in, 1u);
-        uint32_t s = ld(c, bl, cs, cap_b, 4u) & ((1u << H) - 1u);
-        st(c, out, c.lane, cap_out, Qt::G(wd, wd >> (H * Qt::BITS), s), 2u);
     }
     tab_set(c.idxL, d + 1, c.slot);
 }
@@ -475,9 +523,10 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
 // is needed; otherwise the L-th smallest metric value is found with a 32-bit
 // bitonic network and ties at that value are resolved in candidate order.
 __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int &par, int &cand,
-                                          uint32_t &newkey, int &n_keep)
+                                          uint32_t &newkey, int &n_keep, bool &ident)
 {
     const int na = c.n_active, L = c.L;
+    ident = false;
     if (2 * na <= L) {
         n_keep = 2 * na;
         const bool live = c.slot < n_keep;
@@ -502,6 +551,7 @@ __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int 
             par = c.slot;
             cand = 0;
             newkey = ka;
+            ident = true;
             return;
         }
     }
@@ -572,7 +622,8 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
     const uint32_t capd = c.P->lay.b_words[d];
     int par, cand, n_keep;
     uint32_t newkey;
-    if constexpr (M == 2) select_m2(c, kp[0], kp[1], par, cand, newkey, n_keep);
+    bool ident;
+    if constexpr (M == 2) select_m2(c, kp[0], kp[1], par, cand, newkey, n_keep, ident);
     else select_paths<M>(c, kp, par, cand, newkey, n_keep);
     const int pl = c.seg + par;
     // the new path inherits its parent's slot tables (lazy copy)
@@ -638,7 +689,7 @@ __device__ __forceinline__ void op_node(Ctx &c, int d, int type, int side, int t
         V p0 = Qt::zero(), p1 = Qt::zero();
         const int nw = (S + Qt::EPW - 1) / Qt::EPW;
         for (int w = 0; w < nw; ++w) {
-            const uint32_t wd = ld(c, in, w * win + cin, cap_in, 1u);
+            const uint32_t wd = ld(c, in, qa(w, cin, win), cap_in, 1u);
 #pragma unroll
             for (int e = 0; e < Qt::EPW; ++e) {
                 const int i = w * Qt::EPW + e;
@@ -675,7 +726,7 @@ __device__ __forceinline__ void op_node(Ctx &c, int d, int type, int side, int t
     int parity = 0;
     const int nw = (S + Qt::EPW - 1) / Qt::EPW;
     for (int w = 0; w < nw; ++w) {
-        const uint32_t wd = ld(c, in, w * win + cin, cap_in, 1u);
+        const uint32_t wd = ld(c, in, qa(w, cin, win), cap_in, 1u);
 #pragma unroll
         for (int e = 0; e < Qt::EPW; ++e) {
             const int i = w * Qt::EPW + e;
@@ -734,77 +785,92 @@ __device__ __forceinline__ void op_node(Ctx &c, int d, int type, int side, int t
     case 1: PSCL_CANDS(1) break;
     case 2: PSCL_CANDS(2) break;
     case 4: PSCL_CANDS(4) break;
-    case 8: PSCL_CANDS(8) break;
-    default: PSCL_CANDS(16) break;
+    default: PSCL_CANDS(8) break;
     }
 #undef PSCL_CANDS
 }
 
-// A size-2 node whose children are leaves, in registers: f, left leaf, g,
-// right leaf and h of Algorithm 1 in one step.  lfz / rfz: the left / right
-// leaf is frozen.  After a selection the new path takes its parent's two node
-// LLRs and left decision by shuffle (its lazy copy of this node).
-template <class Qt>
-__device__ __forceinline__ void op_pair(Ctx &c, int d, int side, int lfz, int rfz, typename Qt::V &pm)
+// A subtree of S leaves (S = 2..8) with no pruned node, decoded in
+// registers: the f, g, h steps and leaf decisions of Algorithm 1 without
+// touching memory.  a[] holds the node's LLRs.  fz: bit i set = leaf i
+// frozen.  `shuf` moves the register state of the enclosing levels from a
+// parent lane after a selection (the lazy path copy of the register part);
+// when every path keeps its own slot nothing moves.  Returns the node's
+// partial sums (S bits).
+template <class Qt, int S, class Shuf>
+__device__ __forceinline__ uint32_t rsub(Ctx &c, typename Qt::V (&a)[S], uint32_t fz, typename Qt::V &pm,
+                                         const Shuf &shuf)
+{
+    typedef typename Qt::V V;
+    if constexpr (S == 1) {
+        const V lam = a[0];
+        if (fz & 1u) {
+            pm = Qt::add(pm, lam < 0 ? Qt::absv(lam) : Qt::zero());
+            normalise<Qt>(c, pm);
+            return 0u;
+        }
+        int par, cand, nk;
+        uint32_t nkey;
+        bool ident;
+        select_m2(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk, ident);
+        uint32_t hd = (uint32_t)(lam < 0);
+        if (!ident) {
+            const int pl = c.seg + par;
+            c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
+            c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
+            c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
+            c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
+            hd = __shfl_sync(PSCL_FULL, hd, pl);
+            shuf(pl);
+        }
+        pm = Qt::from_key(nkey);
+        c.n_active = nk;
+        normalise<Qt>(c, pm);
+        return hd ^ (uint32_t)cand;
+    } else {
+        constexpr int H = S / 2;
+        V l[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) l[i] = Qt::f1(a[i], a[i + H]);
+        auto shuf_l = [&](int pl) {
+            shuf(pl);
+#pragma unroll
+            for (int i = 0; i < S; ++i) a[i] = __shfl_sync(PSCL_FULL, a[i], pl);
+        };
+        uint32_t bl = rsub<Qt, H>(c, l, fz, pm, shuf_l);
+        V r[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) r[i] = Qt::g1(a[i], a[i + H], (bl >> i) & 1u);
+        auto shuf_r = [&](int pl) {
+            shuf(pl);
+            bl = __shfl_sync(PSCL_FULL, bl, pl);
+        };
+        const uint32_t br = rsub<Qt, H>(c, r, fz >> H, pm, shuf_r);
+        const uint32_t m = (1u << H) - 1u;
+        return ((bl ^ br) & m) | ((br & m) << H);
+    }
+}
+
+template <class Qt, int S>
+__device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, typename Qt::V &pm)
 {
     typedef typename Qt::V V;
     const uint32_t *in = llr_layer(c, d);
     const uint32_t cap = c.P->lay.llr_words[d];
     const int cin = c.seg + tab_get(c.idxL, d);
-    V a0, a1;
-    if (Qt::EPW == 1) {
-        a0 = Qt::elem(ld(c, in, cin, cap, 1u), 0);
-        a1 = Qt::elem(ld(c, in, 32 + cin, cap, 1u), 0);
-    } else {
-        const uint32_t w = ld(c, in, cin, cap, 1u);
-        a0 = Qt::elem(w, 0);
-        a1 = Qt::elem(w, 1);
+    V a[S];
+    constexpr int NW = (S + Qt::EPW - 1) / Qt::EPW;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t wd = ld(c, in, qa(w, cin, 32), cap, 1u);
+#pragma unroll
+        for (int e = 0; e < Qt::EPW; ++e)
+            if (w * Qt::EPW + e < S) a[w * Qt::EPW + e] = Qt::elem(wd, e);
     }
-    // left leaf: LLR f(a0, a1)
-    V lam = Qt::f1(a0, a1);
-    uint32_t uL = 0;
-    if (lfz) {
-        pm = Qt::add(pm, lam < 0 ? Qt::absv(lam) : Qt::zero());
-    } else {
-        int par, cand, nk;
-        uint32_t nkey;
-        select_m2(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk);
-        const int pl = c.seg + par;
-        c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
-        c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
-        c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
-        c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
-        a0 = __shfl_sync(PSCL_FULL, a0, pl);
-        a1 = __shfl_sync(PSCL_FULL, a1, pl);
-        const uint32_t hd = __shfl_sync(PSCL_FULL, (uint32_t)(lam < 0), pl);
-        uL = hd ^ (uint32_t)cand;
-        pm = Qt::from_key(nkey);
-        c.n_active = nk;
-    }
-    normalise<Qt>(c, pm);
-    // right leaf: LLR g(a0, a1, uL)
-    lam = Qt::g1(a0, a1, uL);
-    uint32_t uR = 0;
-    if (rfz) {
-        pm = Qt::add(pm, lam < 0 ? Qt::absv(lam) : Qt::zero());
-    } else {
-        int par, cand, nk;
-        uint32_t nkey;
-        select_m2(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk);
-        const int pl = c.seg + par;
-        c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
-        c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
-        c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
-        c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
-        uL = __shfl_sync(PSCL_FULL, uL, pl);
-        const uint32_t hd = __shfl_sync(PSCL_FULL, (uint32_t)(lam < 0), pl);
-        uR = hd ^ (uint32_t)cand;
-        pm = Qt::from_key(nkey);
-        c.n_active = nk;
-    }
-    normalise<Qt>(c, pm);
+    auto none = [](int) {};
+    const uint32_t beta = rsub<Qt, S>(c, a, fz, pm, none);
     uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
-    st(c, dst, c.lane, c.P->lay.b_words[d], (uL ^ uR) | (uR << 1), 64u);
+    st(c, dst, c.lane, c.P->lay.b_words[d], beta, 64u);
     if (side == 0) tab_set(c.idxS, d, c.slot);
 }
 
@@ -929,7 +995,7 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
                 uint32_t q = Qt::quant(x);
                 word |= Qt::EPW == 1 ? q : (q << (e * Qt::BITS));
             }
-            st(c, l0, row * c.fpw + fr, cap, word, 1024u);
+            st(c, l0, qa(row, fr, c.fpw), cap, word, 1024u);
         }
     }
     __syncwarp();
@@ -945,7 +1011,16 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         case OP_F: op_f<Qt>(c, d); break;
         case OP_G: op_g<Qt>(c, d); break;
         case OP_COMB: op_comb(c, d, op_side(op)); break;
-        case OP_PAIR: op_pair<Qt>(c, d, op_side(op), (int)(op_type(op) & 1u), (int)((op_type(op) >> 1) & 1u), pm); break;
+        case OP_RSUB: {
+            const uint32_t fz = op >> 16;
+            switch (c.N >> d) {
+            case 2: op_rsub<Qt, 2>(c, d, op_side(op), fz, pm); break;
+            case 4: op_rsub<Qt, 4>(c, d, op_side(op), fz, pm); break;
+            case 8: op_rsub<Qt, 8>(c, d, op_side(op), fz, pm); break;
+            default: op_rsub<Qt, 8>(c, d, op_side(op), fz, pm); break;  // host emits S <= 8
+            }
+            break;
+        }
         default: op_node<Qt>(c, d, (int)op_type(op), op_side(op), op_t(op), pm); break;
         }
         __syncwarp();

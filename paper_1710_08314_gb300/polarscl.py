@@ -65,7 +65,13 @@ def lib() -> C.CDLL:
             L.pscl_version.restype = C.c_char_p
             L.pscl_debug_error_word.argtypes = [C.POINTER(u32)]
             L.pscl_set_tuning.argtypes = [i]
+            L.pscl_set_fusion.argtypes = [i]
             _libs[v] = L
+            # optional process-wide tuning overrides (the autotuner sets these per call)
+            if os.environ.get("PSCL_WARPS_PER_SM"):
+                L.pscl_set_tuning(int(os.environ["PSCL_WARPS_PER_SM"]))
+            if os.environ.get("PSCL_FUSE"):
+                L.pscl_set_fusion(int(os.environ["PSCL_FUSE"]))
         return _libs[v]
 
 
@@ -171,6 +177,10 @@ def pscl_debug_last_launches() -> int:
 
 def pscl_set_tuning(target_warps_per_sm: int):
     return _check(lib().pscl_set_tuning(int(target_warps_per_sm)))
+
+
+def pscl_set_fusion(max_leaves: int):
+    return _check(lib().pscl_set_fusion(int(max_leaves)))
 
 
 # ---------------------------------------------------------------------------

@@ -139,4 +139,31 @@ def test_argument_errors():
     with pytest.raises(ps.PsclError):
         g.decode(llr, 3)
     with pytest.raises(ps.PsclError):
-        g.decode(llr, 4, prune=ps.pruning(15, r1_t=7))
+        g.decode(llr, 4, prune=ps.pruning(15, r1_t=4))
+
+
+@pytest.mark.parametrize("fuse", [1, 2, 4, 8])
+def test_every_fusion_depth_gives_identical_results(fuse):
+    """The register-subtree size only changes the schedule, never the result."""
+    from paper_1710_08314_gb300 import polarscl as ps
+    ps.pscl_set_fusion(fuse)
+    try:
+        run_case("c1_cascl_128_64_L4", 300, 1.5, 4, "cascl", "f32", None, 40 + fuse)
+        run_case("mcs_256_128", 200, 1.5, 32, "cascl", "i8", "i8", 50 + fuse)
+        run_case("u09", 200, 1.0, 8, "cascl", "i16", None, 60 + fuse)
+        run_case("c2_2048_1723", 64, 3.5, 16, "cascl", "f32", None, 70 + fuse, frames=np.array([0, 63]))
+    finally:
+        ps.pscl_set_fusion(8)
+
+
+@pytest.mark.parametrize("wps", [4, 16])
+def test_shared_memory_budget_gives_identical_results(wps):
+    """How many warps share an SM decides which layers live in shared memory
+    and which in global scratch; results must not change."""
+    from paper_1710_08314_gb300 import polarscl as ps
+    ps.pscl_set_tuning(wps)
+    try:
+        run_case("c2_2048_1723", 256, 3.5, 32, "cascl", "f32", None, 80 + wps, frames=np.array([5, 255]))
+        run_case("c3_1024_512_L8", 300, 2.0, 8, "cascl", "i8", "i8", 90 + wps, frames=np.arange(0, 300, 37))
+    finally:
+        ps.pscl_set_tuning(8)
