@@ -160,6 +160,49 @@ int pscl_decode_static(pscl_code code, const float *llr, int n_frames, int L, ps
  * one codeword bit (0/1) per byte, punctured positions included.           */
 int pscl_encode(pscl_code code, const uint8_t *info, int n_frames, uint8_t *x_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Uneven batches (many codes, list sizes and number formats at once).
+ * A work item names a code, its frame count, list size, algorithm (PSCL_SC
+ * or PSCL_CASCL), number format and pruning (NULL = none, copied at
+ * pscl_batch_create), and where its frames sit in three caller pools:
+ * llr_offset (floats) of its first LLR row in the LLR pool (rows of N - P
+ * floats), info_offset (bytes) of its first output row in the info pool (rows
+ * of ceil(K_info/8) bytes), status_offset of its first status entry.       */
+typedef struct {
+    pscl_code code;
+    int n_frames;
+    int L;
+    pscl_algo algo;
+    pscl_quant quant;
+    const pscl_pruning *pruning;
+    size_t llr_offset;
+    size_t info_offset;
+    size_t status_offset;
+} pscl_work_item;
+
+typedef struct pscl_batch_s *pscl_batch;
+
+/* Plan a batch: uploads an item table and a task list (a task = 32/L frames
+ * of one item, longest tasks first) and allocates the scratch of every
+ * resident warp.  The codes must outlive the plan.  Allocates (set-up).    */
+int pscl_batch_create(const pscl_work_item *items, int n_items, pscl_batch *out);
+int pscl_batch_destroy(pscl_batch batch);
+
+/* Decode the whole batch: one persistent launch per number format present;
+ * each warp takes the next task from a device counter.  Allocates nothing,
+ * so it can be captured in a CUDA graph and replayed with new pool contents.
+ * Calls of one plan must not overlap (they share its scratch).             */
+int pscl_batch_run(pscl_batch batch, const float *llr_pool, uint8_t *info_pool, int32_t *status_pool,
+                   void *stream);
+
+/* The same decode as one launch per work item (the plain form the persistent
+ * launch is compared with); identical results.                             */
+int pscl_batch_run_plain(pscl_batch batch, const float *llr_pool, uint8_t *info_pool,
+                         int32_t *status_pool, void *stream);
+
+/* Launches per run, total tasks and scratch bytes of a plan.                */
+int pscl_batch_info(pscl_batch batch, int *n_launches, int *n_tasks, size_t *scratch_bytes);
+
 /* Message for the calling thread's most recent error ("" if none).         */
 const char *pscl_last_error(void);
 

@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -76,6 +77,7 @@ static int get_props(DevProps *out)
 // code descriptor
 struct Program {
     uint32_t *d_ops = nullptr;
+    int has_nodes = 0;   // contains pruned-node steps
     int n_ops = 0;
     int max_depth = 0;
     int root_special = 0;
@@ -309,6 +311,8 @@ static int get_program(pscl_code c, const pscl_pruning *pr, Program *out)
     p.n_ops = (int)ops.size();
     p.max_depth = max_depth;
     p.root_special = (op_code(ops[0]) == OP_NODE) ? 1 : 0;
+    for (uint32_t w : ops)
+        if (op_code(w) == OP_NODE) p.has_nodes = 1;
     CU(cudaMalloc(&p.d_ops, ops.size() * sizeof(uint32_t)));
     cudaError_t e = cudaMemcpy(p.d_ops, ops.data(), ops.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -352,9 +356,10 @@ static void make_layout(const pscl_code_s *c, const Program &pg, int L, int quan
     const int fpw = 32 / L;
     uint32_t so = 0, go = 0;
     auto align16 = [](uint32_t v) { return (v + 15u) & ~15u; };
-    // selection scatter (64 words) + frame ids (32 words)
-    lay->src_off = 0;
-    so = align16(96 * 4);
+    // the warp's copy of its Item, then the selection scatter (64 words) and
+    // frame ids (32 words)
+    lay->src_off = kItemBytes + kPtabBytes;
+    so = align16(lay->src_off + 96 * 4);
     const int maxd = pg.max_depth;
     for (int d = maxd; d >= 0; d--) {
         const int S = c->N >> d;
@@ -415,6 +420,7 @@ struct Plan {
     int total_warps = 0;
     size_t smem_block = 0;
     size_t gmem_scratch = 0;   // per-warp slices
+    uint32_t gmem_per_warp = 0;
     size_t list_bytes = 0;     // adaptive frame lists + counters
     size_t total_ws = 0;
     int n_stages = 0;
@@ -470,7 +476,7 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     }
     pl->smem_block = (size_t)max_smem * kWarpsPerBlock;
     int bps = 0;
-    cudaError_t e = scl_func_attrs((int)quant, pl->smem_block, 32 * kWarpsPerBlock, &bps);
+    cudaError_t e = scl_func_attrs((int)quant, pl->pg.has_nodes != 0, pl->smem_block, 32 * kWarpsPerBlock, &bps);
     if (e != cudaSuccess) return fail(PSCL_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     if (bps < 1) return fail(PSCL_EUNSUPPORTED, "no block fits (shared memory %zu bytes)", pl->smem_block);
     const int max_warps = dp.sms * bps * kWarpsPerBlock;
@@ -484,6 +490,7 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     int tw = (int)(want < max_warps ? want : max_warps);
     pl->grid = (tw + kWarpsPerBlock - 1) / kWarpsPerBlock;
     pl->total_warps = pl->grid * kWarpsPerBlock;
+    pl->gmem_per_warp = max_gmem;
     pl->gmem_scratch = (size_t)max_gmem * (size_t)pl->total_warps;
     pl->list_bytes = pl->n_stages > 1 ? (2 * (size_t)n_frames * 4 + 256 + 255) & ~(size_t)255 : 0;
     pl->total_ws = 256 /* error word + counters */ + pl->list_bytes + pl->gmem_scratch;
@@ -501,11 +508,11 @@ extern "C" int pscl_workspace_size(pscl_code c, int n_frames, int L, pscl_algo a
     return PSCL_OK;
 }
 
-static cudaError_t launch_stage(int quant, const KParams &kp, int grid, size_t smem, cudaStream_t s)
+static cudaError_t launch_stage(int quant, bool nodes, const KParams &kp, int grid, size_t smem, cudaStream_t s)
 {
-    if (quant == PSCL_F32) return launch_scl_f32(kp, grid, 32 * kWarpsPerBlock, smem, s);
-    if (quant == PSCL_I16) return launch_scl_i16(kp, grid, 32 * kWarpsPerBlock, smem, s);
-    return launch_scl_i8(kp, grid, 32 * kWarpsPerBlock, smem, s);
+    if (quant == PSCL_F32) return launch_scl_f32(kp, nodes, grid, 32 * kWarpsPerBlock, smem, s);
+    if (quant == PSCL_I16) return launch_scl_i16(kp, nodes, grid, 32 * kWarpsPerBlock, smem, s);
+    return launch_scl_i8(kp, nodes, grid, 32 * kWarpsPerBlock, smem, s);
 }
 
 static int g_last_launches = 0;
@@ -534,37 +541,37 @@ static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_a
         const int Ls = pl.stages[s];
         KParams kp;
         memset(&kp, 0, sizeof(kp));
-        kp.code = c->dc;
-        kp.ops = pl.pg.d_ops;
-        kp.n_ops = pl.pg.n_ops;
-        kp.root_special = pl.pg.root_special;
-        make_layout(c, pl.pg, Ls, (int)quant, budget, &kp.lay);
-        kp.llr = llr;
-        kp.n_frames = n_frames;
-        kp.L = Ls;
-        kp.L_out = L;
-        kp.stage_L = Ls;
-        kp.info_out = info_out;
-        kp.status_out = status_out;
-        kp.pm_out = pm_out;
+        Item &it = kp.single;
+        it.code = c->dc;
+        it.ops = pl.pg.d_ops;
+        it.n_ops = pl.pg.n_ops;
+        it.root_special = pl.pg.root_special;
+        make_layout(c, pl.pg, Ls, (int)quant, budget, &it.lay);
+        it.llr = llr;
+        it.n_frames = n_frames;
+        it.L = Ls;
+        it.L_out = L;
+        it.stage_L = Ls;
+        it.info_out = info_out;
+        it.status_out = status_out;
+        it.pm_out = pm_out;
+        it.err = err;
         kp.gmem = gmem;
+        kp.gmem_per_warp = pl.gmem_per_warp;
+        kp.smem_per_warp = it.lay.smem_per_warp;
         kp.total_warps = pl.total_warps;
-        kp.err = err;
         const bool last = s == pl.n_stages - 1;
-        if (s == 0) {
-            kp.frame_list = nullptr;
-            kp.list_count = nullptr;
-        } else {
-            kp.frame_list = lists + (size_t)((s - 1) & 1) * (size_t)n_frames;
-            kp.list_count = counts + ((s - 1) & 1);
+        if (s > 0) {
+            it.frame_list = lists + (size_t)((s - 1) & 1) * (size_t)n_frames;
+            it.list_count = counts + ((s - 1) & 1);
         }
         if (!last) {
-            kp.next_list = lists + (size_t)(s & 1) * (size_t)n_frames;
-            kp.next_count = counts + (s & 1);
-            CU(cudaMemsetAsync(kp.next_count, 0, sizeof(int32_t), stream));
+            it.next_list = lists + (size_t)(s & 1) * (size_t)n_frames;
+            it.next_count = counts + (s & 1);
+            CU(cudaMemsetAsync(it.next_count, 0, sizeof(int32_t), stream));
         }
-        const size_t smem = (size_t)kp.lay.smem_per_warp * kWarpsPerBlock;
-        cudaError_t e = launch_stage((int)quant, kp, pl.grid, smem, stream);
+        const size_t smem = (size_t)it.lay.smem_per_warp * kWarpsPerBlock;
+        cudaError_t e = launch_stage((int)quant, pl.pg.has_nodes != 0, kp, pl.grid, smem, stream);
         if (e != cudaSuccess) return fail(PSCL_ECUDA, "decode launch: %s", cudaGetErrorString(e));
         launches++;
     }
@@ -742,4 +749,256 @@ extern "C" int pscl_decode_static(pscl_code c, const float *llr, int n_frames, i
     CU(cudaMemsetAsync(ws, 0, 256, (cudaStream_t)stream));
     return run_decode(c, llr, n_frames, L, algo, pr, quant, info_out, status_out, pm_out, ws,
                       PSCL_STATIC_SCRATCH_BYTES, (cudaStream_t)stream, pl);
+}
+
+// ---------------------------------------------------------------------------
+// Uneven batches: many work items (codes, list sizes, number formats) in one
+// persistent launch per number format.  The plan owns a device item table, a
+// task list sorted longest-first, a task counter and the warps' scratch, so
+// running it allocates nothing and can be captured in a CUDA graph.
+struct BatchGroup {
+    int quant = 0;
+    bool nodes = false;
+    int n_tasks = 0;
+    int grid = 0;
+    int total_warps = 0;
+    size_t smem_block = 0;
+    uint32_t smem_per_warp = 0, gmem_per_warp = 0;
+    int2 *d_tasks = nullptr;
+    int *d_ctr = nullptr;
+    char *d_gmem = nullptr;
+    std::vector<int> items;          // item indices of this group
+    std::vector<std::vector<int2>> item_tasks;
+};
+
+struct pscl_batch_s {
+    int dev = -1;
+    std::vector<pscl_work_item> wi;
+    std::vector<Item> h_items;
+    Item *d_items = nullptr;
+    uint32_t *d_err = nullptr;
+    std::vector<BatchGroup> groups;
+    std::vector<void *> allocs;
+};
+
+static void batch_free(pscl_batch b)
+{
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+extern "C" int pscl_batch_create(const pscl_work_item *items, int n_items, pscl_batch *out)
+{
+    if (!out) return fail(PSCL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!items || n_items < 1) return fail(PSCL_EINVAL, "no work items");
+    DevProps dp;
+    int rc = get_props(&dp);
+    if (rc) return rc;
+    int dev;
+    CU(cudaGetDevice(&dev));
+    pscl_batch b = new pscl_batch_s();
+    b->dev = dev;
+    b->wi.assign(items, items + n_items);
+    b->h_items.resize((size_t)n_items);
+    std::vector<Program> progs((size_t)n_items);
+    for (int i = 0; i < n_items; i++) {
+        const pscl_work_item &w = items[i];
+        if (!w.code || w.code->dev != dev) { batch_free(b); return fail(PSCL_EINVAL, "item %d: bad code", i); }
+        if (w.algo != PSCL_SC && w.algo != PSCL_CASCL) {
+            batch_free(b);
+            return fail(PSCL_EUNSUPPORTED, "item %d: batches take SC or CASCL items", i);
+        }
+        if (w.L != 1 && w.L != 2 && w.L != 4 && w.L != 8 && w.L != 16 && w.L != 32) {
+            batch_free(b);
+            return fail(PSCL_EINVAL, "item %d: L=%d", i, w.L);
+        }
+        if (w.quant < PSCL_F32 || w.quant > PSCL_I8 || w.n_frames < 0) {
+            batch_free(b);
+            return fail(PSCL_EINVAL, "item %d: bad quantisation or frame count", i);
+        }
+        rc = get_program(w.code, w.pruning, &progs[(size_t)i]);
+        if (rc) { batch_free(b); return rc; }
+    }
+    void *p;
+    cudaError_t e = cudaMalloc(&p, 256);
+    if (e != cudaSuccess) { batch_free(b); return fail(PSCL_ENOMEM, "batch: %s", cudaGetErrorString(e)); }
+    b->allocs.push_back(p);
+    b->d_err = (uint32_t *)p;
+    cudaMemset(p, 0, 256);
+    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
+    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
+    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    for (int q = PSCL_F32; q <= PSCL_I8; q++) {
+        BatchGroup g;
+        g.quant = q;
+        std::vector<std::pair<double, int2>> tasks;
+        for (int i = 0; i < n_items; i++) {
+            const pscl_work_item &w = items[i];
+            if ((int)w.quant != q || w.n_frames == 0) continue;
+            const int L = w.algo == PSCL_SC ? 1 : w.L;
+            Item &it = b->h_items[(size_t)i];
+            memset(&it, 0, sizeof(it));
+            it.code = w.code->dc;
+            it.ops = progs[(size_t)i].d_ops;
+            it.n_ops = progs[(size_t)i].n_ops;
+            it.root_special = progs[(size_t)i].root_special;
+            make_layout(w.code, progs[(size_t)i], L, q, budget, &it.lay);
+            it.llr_off = w.llr_offset;
+            it.info_off = w.info_offset;
+            it.status_off = (int)w.status_offset;
+            it.n_frames = w.n_frames;
+            it.L = L;
+            it.L_out = L;
+            it.stage_L = L;
+            it.err = b->d_err;
+            if (progs[(size_t)i].has_nodes) g.nodes = true;
+            if (it.lay.smem_per_warp > g.smem_per_warp) g.smem_per_warp = it.lay.smem_per_warp;
+            if (it.lay.gmem_per_warp > g.gmem_per_warp) g.gmem_per_warp = it.lay.gmem_per_warp;
+            g.items.push_back(i);
+            // a task decodes 32/L frames of one item; cost ~ N log N grows
+            // with the list size through the selections
+            const int fpw = 32 / L;
+            const double cost = (double)w.code->N * (double)(w.code->n) * (1.0 + 0.25 * __builtin_ctz((unsigned)L));
+            for (int f = 0; f < w.n_frames; f += fpw) tasks.push_back({cost, make_int2(i, f)});
+        }
+        if (tasks.empty()) continue;
+        std::stable_sort(tasks.begin(), tasks.end(),
+                         [](const std::pair<double, int2> &a, const std::pair<double, int2> &b2) { return a.first > b2.first; });
+        std::vector<int2> h_tasks(tasks.size());
+        for (size_t k = 0; k < tasks.size(); k++) h_tasks[k] = tasks[k].second;
+        g.n_tasks = (int)h_tasks.size();
+        g.smem_block = (size_t)g.smem_per_warp * kWarpsPerBlock;
+        int bps = 0;
+        e = scl_func_attrs(q, g.nodes, g.smem_block, 32 * kWarpsPerBlock, &bps);
+        if (e != cudaSuccess || bps < 1) {
+            batch_free(b);
+            return fail(PSCL_EUNSUPPORTED, "batch: no block fits (%zu bytes of shared memory)", g.smem_block);
+        }
+        const int max_warps = dp.sms * bps * kWarpsPerBlock;
+        const int tw = g.n_tasks < max_warps ? g.n_tasks : max_warps;
+        g.grid = (tw + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        g.total_warps = g.grid * kWarpsPerBlock;
+        e = cudaMalloc(&p, sizeof(int2) * h_tasks.size());
+        if (e == cudaSuccess) {
+            b->allocs.push_back(p);
+            g.d_tasks = (int2 *)p;
+            e = cudaMemcpy(p, h_tasks.data(), sizeof(int2) * h_tasks.size(), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) {
+            e = cudaMalloc(&p, 256 + (size_t)g.gmem_per_warp * (size_t)g.total_warps);
+            if (e == cudaSuccess) {
+                b->allocs.push_back(p);
+                g.d_ctr = (int *)p;
+                g.d_gmem = (char *)p + 256;
+            }
+        }
+        if (e != cudaSuccess) {
+            batch_free(b);
+            return fail(PSCL_ENOMEM, "batch: %s", cudaGetErrorString(e));
+        }
+        // per-item task lists for the one-launch-per-item form
+        g.item_tasks.resize(g.items.size());
+        b->groups.push_back(g);
+    }
+    e = cudaMalloc(&p, sizeof(Item) * (size_t)n_items);
+    if (e == cudaSuccess) {
+        b->allocs.push_back(p);
+        b->d_items = (Item *)p;
+        e = cudaMemcpy(p, b->h_items.data(), sizeof(Item) * (size_t)n_items, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return fail(PSCL_ENOMEM, "batch: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_destroy(pscl_batch b)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    batch_free(b);
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_run(pscl_batch b, const float *llr_pool, uint8_t *info_pool, int32_t *status_pool,
+                              void *stream)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    if (!llr_pool || !info_pool || !status_pool) return fail(PSCL_EINVAL, "pools are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    int launches = 0;
+    for (const BatchGroup &g : b->groups) {
+        KParams kp;
+        memset(&kp, 0, sizeof(kp));
+        kp.items = b->d_items;
+        kp.tasks = g.d_tasks;
+        kp.n_tasks = g.n_tasks;
+        kp.task_ctr = g.d_ctr;
+        kp.gmem = g.d_gmem;
+        kp.gmem_per_warp = g.gmem_per_warp;
+        kp.smem_per_warp = g.smem_per_warp;
+        kp.total_warps = g.total_warps;
+        kp.llr_pool = llr_pool;
+        kp.info_pool = info_pool;
+        kp.status_pool = status_pool;
+        CU(cudaMemsetAsync(g.d_ctr, 0, sizeof(int), s));
+        cudaError_t e = launch_stage(g.quant, g.nodes, kp, g.grid, g.smem_block, s);
+        if (e != cudaSuccess) return fail(PSCL_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+        launches++;
+    }
+    g_last_launches = launches;
+    return PSCL_OK;
+}
+
+// The same batch decoded one launch per work item (no overlap between items,
+// no task counter): the plain form the persistent launch is measured against.
+extern "C" int pscl_batch_run_plain(pscl_batch b, const float *llr_pool, uint8_t *info_pool,
+                                    int32_t *status_pool, void *stream)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    if (!llr_pool || !info_pool || !status_pool) return fail(PSCL_EINVAL, "pools are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    int launches = 0;
+    for (const BatchGroup &g : b->groups) {
+        for (int i : g.items) {
+            const pscl_work_item &w = b->wi[(size_t)i];
+            KParams kp;
+            memset(&kp, 0, sizeof(kp));
+            kp.single = b->h_items[(size_t)i];
+            kp.single.llr = llr_pool + w.llr_offset;
+            kp.single.info_out = info_pool + w.info_offset;
+            kp.single.status_out = status_pool + w.status_offset;
+            kp.single.pm_out = nullptr;
+            const int fpw = 32 / kp.single.L;
+            const int tasks = (w.n_frames + fpw - 1) / fpw;
+            const int tw = tasks < g.total_warps ? tasks : g.total_warps;
+            const int grid = (tw + kWarpsPerBlock - 1) / kWarpsPerBlock;
+            kp.gmem = g.d_gmem;
+            kp.gmem_per_warp = g.gmem_per_warp;
+            kp.smem_per_warp = kp.single.lay.smem_per_warp;
+            kp.total_warps = grid * kWarpsPerBlock;
+            cudaError_t e = launch_stage(g.quant, g.nodes, kp, grid, (size_t)kp.smem_per_warp * kWarpsPerBlock, s);
+            if (e != cudaSuccess) return fail(PSCL_ECUDA, "plain launch: %s", cudaGetErrorString(e));
+            launches++;
+        }
+    }
+    g_last_launches = launches;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_batch_info(pscl_batch b, int *n_launches, int *n_tasks, size_t *scratch_bytes)
+{
+    if (!b) return fail(PSCL_EINVAL, "batch is NULL");
+    int t = 0;
+    size_t bytes = 0;
+    for (const BatchGroup &g : b->groups) {
+        t += g.n_tasks;
+        bytes += (size_t)g.gmem_per_warp * (size_t)g.total_warps;
+    }
+    if (n_launches) *n_launches = (int)b->groups.size();
+    if (n_tasks) *n_tasks = t;
+    if (scratch_bytes) *scratch_bytes = bytes;
+    return PSCL_OK;
 }

@@ -61,14 +61,19 @@ struct Layout {
     uint32_t gmem_per_warp;
 };
 
-struct KParams {
+// One decode work item: a code, its node schedule and memory layout, a list
+// size, and where its frames' inputs and outputs sit.  Every warp copies the
+// item of its current task into the head of its shared-memory slice.
+struct Item {
     DevCode code;
     const uint32_t *ops;
     int n_ops;
     int root_special;
     Layout lay;
-    const float *llr;
-    int n_frames;               // frames in the batch (rows of llr / outputs)
+    size_t llr_off;             // batch: offset of the item's first LLR (floats)
+    size_t info_off;            // batch: offset of its first info byte
+    int status_off;             // batch: index of its first status entry
+    int n_frames;               // frames of the item (rows of llr / outputs)
     int L;                      // list size of this stage
     int L_out;                  // pm_out row length
     int stage_L;                // reported in status bits 8..15
@@ -76,19 +81,39 @@ struct KParams {
     const int32_t *list_count;  // with frame_list: device count of ids
     int32_t *next_list;         // adaptive: failed frames are appended here
     int32_t *next_count;        //   (NULL when this is the last stage)
+    const float *llr;
     uint8_t *info_out;
     int32_t *status_out;
     float *pm_out;
-    char *gmem;                 // global scratch base
-    int total_warps;
     uint32_t *err;              // debug error word (checked builds)
 };
 
+// bytes reserved at the head of each warp's shared slice for its Item copy,
+// followed by the table of its 36 buffer pointers
+constexpr uint32_t kItemBytes = (uint32_t)((sizeof(Item) + 15) / 16 * 16);
+constexpr uint32_t kPtabBytes = 3 * kMaxLayers * 8;
+
+struct KParams {
+    Item single;                // the item when tasks == NULL
+    const Item *items;          // batch: device item table
+    const int2 *tasks;          // batch: (item, first frame) per task, NULL = single item
+    int n_tasks;
+    int *task_ctr;              // batch: next task (zeroed before the launch)
+    char *gmem;                 // global scratch base
+    uint32_t gmem_per_warp;
+    uint32_t smem_per_warp;
+    int total_warps;
+    const float *llr_pool;      // batch pools (items add their offsets)
+    uint8_t *info_pool;
+    int32_t *status_pool;
+};
+
 // launchers, one per number format (defined in scl_*.cu)
-cudaError_t launch_scl_f32(const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_scl_i16(const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_scl_i8(const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t scl_func_attrs(int quant, size_t smem, int block, int *blocks_per_sm);
+// nodes: the schedule contains pruned nodes (R0/R1/REP/SPC steps)
+cudaError_t launch_scl_f32(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_scl_i16(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_scl_i8(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t scl_func_attrs(int quant, bool nodes, size_t smem, int block, int *blocks_per_sm);
 
 struct EncParams {
     DevCode code;

@@ -1,4 +1,5 @@
-// scl_f32.cu -- instantiation of the SCL kernel for the f32 number format.
+// scl_f32.cu -- instantiations of the SCL kernel for the f32 number format
+// (with and without the pruned-node handlers).
 #include <map>
 #include <mutex>
 
@@ -7,7 +8,7 @@
 namespace pscl {
 
 static std::mutex g_attr_mu_f32;
-static std::map<int, bool> g_attr_set_f32;
+static std::map<int, int> g_attr_set_f32;
 
 static cudaError_t ensure_attr_f32()
 {
@@ -19,24 +20,28 @@ static cudaError_t ensure_attr_f32()
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(scl_kernel<QF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) g_attr_set_f32[dev] = true;
+    e = cudaFuncSetAttribute(scl_kernel<QF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(scl_kernel<QF32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) g_attr_set_f32[dev] = 1;
     return e;
 }
 
-cudaError_t launch_scl_f32(const KParams &p, int grid, int block, size_t smem, cudaStream_t s)
+cudaError_t launch_scl_f32(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s)
 {
     cudaError_t e = ensure_attr_f32();
     if (e != cudaSuccess) return e;
-    scl_kernel<QF32><<<grid, block, smem, s>>>(p);
+    if (nodes) scl_kernel<QF32, true><<<grid, block, smem, s>>>(p);
+    else scl_kernel<QF32, false><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t scl_attrs_f32(size_t smem, int block, int *bps)
+cudaError_t scl_attrs_f32(bool nodes, size_t smem, int block, int *bps)
 {
     cudaError_t e = ensure_attr_f32();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QF32>, block, smem);
+    if (nodes) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QF32, true>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QF32, false>, block, smem);
 }
 
 }  // namespace pscl

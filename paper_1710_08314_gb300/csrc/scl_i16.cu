@@ -1,4 +1,5 @@
-// scl_i16.cu -- instantiation of the SCL kernel for the i16 number format.
+// scl_i16.cu -- instantiations of the SCL kernel for the i16 number format
+// (with and without the pruned-node handlers).
 #include <map>
 #include <mutex>
 
@@ -7,7 +8,7 @@
 namespace pscl {
 
 static std::mutex g_attr_mu_i16;
-static std::map<int, bool> g_attr_set_i16;
+static std::map<int, int> g_attr_set_i16;
 
 static cudaError_t ensure_attr_i16()
 {
@@ -19,24 +20,28 @@ static cudaError_t ensure_attr_i16()
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(scl_kernel<QI16>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) g_attr_set_i16[dev] = true;
+    e = cudaFuncSetAttribute(scl_kernel<QI16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(scl_kernel<QI16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) g_attr_set_i16[dev] = 1;
     return e;
 }
 
-cudaError_t launch_scl_i16(const KParams &p, int grid, int block, size_t smem, cudaStream_t s)
+cudaError_t launch_scl_i16(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s)
 {
     cudaError_t e = ensure_attr_i16();
     if (e != cudaSuccess) return e;
-    scl_kernel<QI16><<<grid, block, smem, s>>>(p);
+    if (nodes) scl_kernel<QI16, true><<<grid, block, smem, s>>>(p);
+    else scl_kernel<QI16, false><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t scl_attrs_i16(size_t smem, int block, int *bps)
+cudaError_t scl_attrs_i16(bool nodes, size_t smem, int block, int *bps)
 {
     cudaError_t e = ensure_attr_i16();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QI16>, block, smem);
+    if (nodes) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QI16, true>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QI16, false>, block, smem);
 }
 
 }  // namespace pscl

@@ -1,4 +1,5 @@
-// scl_i8.cu -- instantiation of the SCL kernel for the i8 number format.
+// scl_i8.cu -- instantiations of the SCL kernel for the i8 number format
+// (with and without the pruned-node handlers).
 #include <map>
 #include <mutex>
 
@@ -7,7 +8,7 @@
 namespace pscl {
 
 static std::mutex g_attr_mu_i8;
-static std::map<int, bool> g_attr_set_i8;
+static std::map<int, int> g_attr_set_i8;
 
 static cudaError_t ensure_attr_i8()
 {
@@ -19,24 +20,28 @@ static cudaError_t ensure_attr_i8()
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(scl_kernel<QI8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) g_attr_set_i8[dev] = true;
+    e = cudaFuncSetAttribute(scl_kernel<QI8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(scl_kernel<QI8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) g_attr_set_i8[dev] = 1;
     return e;
 }
 
-cudaError_t launch_scl_i8(const KParams &p, int grid, int block, size_t smem, cudaStream_t s)
+cudaError_t launch_scl_i8(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s)
 {
     cudaError_t e = ensure_attr_i8();
     if (e != cudaSuccess) return e;
-    scl_kernel<QI8><<<grid, block, smem, s>>>(p);
+    if (nodes) scl_kernel<QI8, true><<<grid, block, smem, s>>>(p);
+    else scl_kernel<QI8, false><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t scl_attrs_i8(size_t smem, int block, int *bps)
+cudaError_t scl_attrs_i8(bool nodes, size_t smem, int block, int *bps)
 {
     cudaError_t e = ensure_attr_i8();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QI8>, block, smem);
+    if (nodes) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QI8, true>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, scl_kernel<QI8, false>, block, smem);
 }
 
 }  // namespace pscl

@@ -32,7 +32,7 @@ namespace pscl {
 //   f(a, b) = sign(a b) min(|a|, |b|)      g(a, b, s) = (1 - 2s) a + b
 // with the sign of f taken from the sign bits and g computed as (s?-a:a)+b.
 struct QF32 {
-    static constexpr int EPW = 1, BITS = 32, FIXED = 0;
+    static constexpr int EPW = 1, BITS = 32, FIXED = 0, VBITS = 0;
     typedef float V;
     __device__ static __forceinline__ uint32_t F(uint32_t a, uint32_t b)
     {
@@ -59,7 +59,7 @@ struct QF32 {
 };
 
 struct QI16 {
-    static constexpr int EPW = 2, BITS = 16, FIXED = 1, Q = 32767, FRAC = 5;
+    static constexpr int EPW = 2, BITS = 16, FIXED = 1, Q = 32767, FRAC = 5, VBITS = 15;
     typedef int V;
     __device__ static __forceinline__ uint32_t F(uint32_t a, uint32_t b)
     {
@@ -101,7 +101,7 @@ struct QI16 {
 };
 
 struct QI8 {
-    static constexpr int EPW = 4, BITS = 8, FIXED = 1, Q = 127, FRAC = 2;
+    static constexpr int EPW = 4, BITS = 8, FIXED = 1, Q = 127, FRAC = 2, VBITS = 7;
     typedef int V;
     __device__ static __forceinline__ uint32_t F(uint32_t a, uint32_t b)
     {
@@ -145,12 +145,14 @@ struct QI8 {
 // ---------------------------------------------------------------------------
 // Warp context
 struct Ctx {
-    const KParams *P;
+    const Item *P;   // the current task's item (shared-memory copy)
     char *sm;        // warp's shared slice
     char *gm;        // warp's global scratch slice
     int lane, L, seg, slot, fpw, fiw;
     int N, n;
     int n_active;    // warp-uniform
+    const uint32_t *ops;
+    int n_ops;
     uint32_t idxL[2], idxS[2];  // per-layer slot tables, 6 x 5 bits per word
 };
 
@@ -187,21 +189,13 @@ __device__ __forceinline__ bool chk(const Ctx &c, bool ok, uint32_t code)
 #define PSCL_OK_IDX(c, idx, cap, code) true
 #endif
 
-__device__ __forceinline__ uint32_t *llr_layer(const Ctx &c, int d)
-{
-    char *b = ((c.P->lay.llr_smem >> d) & 1u) ? c.sm : c.gm;
-    return (uint32_t *)(b + c.P->lay.llr_off[d]);
-}
-__device__ __forceinline__ uint32_t *bl_layer(const Ctx &c, int d)
-{
-    char *b = ((c.P->lay.bl_smem >> d) & 1u) ? c.sm : c.gm;
-    return (uint32_t *)(b + c.P->lay.bl_off[d]);
-}
-__device__ __forceinline__ uint32_t *br_layer(const Ctx &c, int d)
-{
-    char *b = ((c.P->lay.br_smem >> d) & 1u) ? c.sm : c.gm;
-    return (uint32_t *)(b + c.P->lay.br_off[d]);
-}
+// Base pointers of every buffer of the warp, computed once per item and kept
+// in a small table behind the item copy: [0..11] LLR layers, [12..23] BL,
+// [24..35] BR.
+__device__ __forceinline__ uint32_t **ptab(const Ctx &c) { return (uint32_t **)(c.sm + kItemBytes); }
+__device__ __forceinline__ uint32_t *llr_layer(const Ctx &c, int d) { return ptab(c)[d]; }
+__device__ __forceinline__ uint32_t *bl_layer(const Ctx &c, int d) { return ptab(c)[kMaxLayers + d]; }
+__device__ __forceinline__ uint32_t *br_layer(const Ctx &c, int d) { return ptab(c)[2 * kMaxLayers + d]; }
 
 // LLR layers store the words of a path in groups of four: word w of column
 // col sits at ((w / 4) * width + col) * 4 + w % 4, so a lane moves four
@@ -522,6 +516,7 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
 // every first candidate, the first candidates are the survivors and no sort
 // is needed; otherwise the L-th smallest metric value is found with a 32-bit
 // bitonic network and ties at that value are resolved in candidate order.
+template <int VBITS>
 __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int &par, int &cand,
                                           uint32_t &newkey, int &n_keep, bool &ident)
 {
@@ -555,29 +550,44 @@ __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int 
             return;
         }
     }
-    // L-th smallest metric value: bitonic sort of 2L values, element e = 2*slot + m
-    uint32_t k0 = a, k1 = b;
-    for (int size = 2; size <= 2 * L; size <<= 1) {
-        const bool up = ((c.slot << 1) & size) == 0;
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride == 1) {
-                const uint32_t lo = min(k0, k1), hi = max(k0, k1);
-                k0 = up ? lo : hi;
-                k1 = up ? hi : lo;
-            } else {
-                const int ls = stride >> 1;
-                const bool takemin = ((c.slot & ls) == 0) == up;
-                const uint32_t o0 = __shfl_xor_sync(PSCL_FULL, k0, ls);
-                const uint32_t o1 = __shfl_xor_sync(PSCL_FULL, k1, ls);
-                k0 = takemin ? min(k0, o0) : max(k0, o0);
-                k1 = takemin ? min(k1, o1) : max(k1, o1);
+    const uint32_t segmask = L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << c.seg);
+    uint32_t tau;
+    if constexpr (VBITS > 0) {
+        // fixed point: metrics are integers below 2^VBITS, so the L-th
+        // smallest value is found by bisection on its bits (ballot counts)
+        uint32_t v = 0;
+#pragma unroll
+        for (int bit = VBITS - 1; bit >= 0; --bit) {
+            const uint32_t cand = v | ((1u << bit) - 1u);
+            const int cnt = __popc(__ballot_sync(PSCL_FULL, a <= cand) & segmask) +
+                            __popc(__ballot_sync(PSCL_FULL, b <= cand) & segmask);
+            if (cnt < L) v |= 1u << bit;
+        }
+        tau = v;
+    } else {
+        // float: bitonic sort of the 2L metric patterns, element e = 2*slot + m
+        uint32_t k0 = a, k1 = b;
+        for (int size = 2; size <= 2 * L; size <<= 1) {
+            const bool up = ((c.slot << 1) & size) == 0;
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                if (stride == 1) {
+                    const uint32_t lo = min(k0, k1), hi = max(k0, k1);
+                    k0 = up ? lo : hi;
+                    k1 = up ? hi : lo;
+                } else {
+                    const int ls = stride >> 1;
+                    const bool takemin = ((c.slot & ls) == 0) == up;
+                    const uint32_t o0 = __shfl_xor_sync(PSCL_FULL, k0, ls);
+                    const uint32_t o1 = __shfl_xor_sync(PSCL_FULL, k1, ls);
+                    k0 = takemin ? min(k0, o0) : max(k0, o0);
+                    k1 = takemin ? min(k1, o1) : max(k1, o1);
+                }
             }
         }
+        const int tp = (L - 1) >> 1;
+        const uint32_t tsel = ((L - 1) & 1) ? k1 : k0;
+        tau = __shfl_sync(PSCL_FULL, tsel, c.seg + tp);
     }
-    const int tp = (L - 1) >> 1;
-    const uint32_t tsel = ((L - 1) & 1) ? k1 : k0;
-    const uint32_t tau = __shfl_sync(PSCL_FULL, tsel, c.seg + tp);
-    const uint32_t segmask = L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << c.seg);
     const uint32_t lt = ((1u << c.lane) - 1u) & segmask;
     const uint32_t BA = __ballot_sync(PSCL_FULL, a < tau) & segmask;
     const uint32_t BB = __ballot_sync(PSCL_FULL, b < tau) & segmask;
@@ -623,7 +633,7 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
     int par, cand, n_keep;
     uint32_t newkey;
     bool ident;
-    if constexpr (M == 2) select_m2(c, kp[0], kp[1], par, cand, newkey, n_keep, ident);
+    if constexpr (M == 2) select_m2<Qt::VBITS>(c, kp[0], kp[1], par, cand, newkey, n_keep, ident);
     else select_paths<M>(c, kp, par, cand, newkey, n_keep);
     const int pl = c.seg + par;
     // the new path inherits its parent's slot tables (lazy copy)
@@ -812,7 +822,7 @@ __device__ __forceinline__ uint32_t rsub(Ctx &c, typename Qt::V (&a)[S], uint32_
         int par, cand, nk;
         uint32_t nkey;
         bool ident;
-        select_m2(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk, ident);
+        select_m2<Qt::VBITS>(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk, ident);
         uint32_t hd = (uint32_t)(lam < 0);
         if (!ident) {
             const int pl = c.seg + par;
@@ -879,7 +889,7 @@ __device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, ty
 // with its BL_1 column `cl`) once the root is complete
 __device__ __forceinline__ uint32_t xhat_word(const Ctx &c, int w, int col, int cl)
 {
-    const KParams &P = *c.P;
+    const Item &P = *c.P;
     if (P.root_special) return ld(c, br_layer(c, 0), w * 32 + col, P.lay.b_words[0], 256u);
     const int half = c.N >> 1;
     const uint32_t *bl = bl_layer(c, 1), *br = br_layer(c, 1);
@@ -961,11 +971,11 @@ static __device__ bool crc_check(const Ctx &c, int cl)
 
 // ---------------------------------------------------------------------------
 // Decode the frames of one task: list positions [pos0, pos0 + 32/L).
-template <class Qt>
+template <class Qt, bool NODES>
 __device__ void decode_task(Ctx &c, int pos0, int count)
 {
     typedef typename Qt::V V;
-    const KParams &P = *c.P;
+    const Item &P = *c.P;
     const DevCode &cd = P.code;
     int32_t *fids = (int32_t *)(c.sm + P.lay.src_off) + 64;  // 32 frame ids
     // frame id of this lane's frame (-1: none)
@@ -1004,8 +1014,8 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     tab_fill(c.idxS, c.slot);
     V pm = Qt::zero();
     // walk the node schedule
-    for (int i = 0; i < P.n_ops; ++i) {
-        const uint32_t op = __ldg(&P.ops[i]);
+    for (int i = 0; i < c.n_ops; ++i) {
+        const uint32_t op = __ldg(&c.ops[i]);
         const int d = op_depth(op);
         switch (op_code(op)) {
         case OP_F: op_f<Qt>(c, d); break;
@@ -1021,7 +1031,9 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
             }
             break;
         }
-        default: op_node<Qt>(c, d, (int)op_type(op), op_side(op), op_t(op), pm); break;
+        default:
+            if constexpr (NODES) op_node<Qt>(c, d, (int)op_type(op), op_side(op), op_t(op), pm);
+            break;
         }
         __syncwarp();
     }
@@ -1074,28 +1086,83 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     __syncwarp();
 }
 
-template <class Qt>
-__global__ void __launch_bounds__(128) scl_kernel(const __grid_constant__ KParams P)
+// copy an item into the warp's shared slice and set the lane roles
+__device__ __forceinline__ void load_item(Ctx &c, const Item *src, const KParams &K, bool batch)
+{
+    uint32_t *dst = (uint32_t *)c.sm;
+    const uint32_t *from = (const uint32_t *)src;
+    __syncwarp();
+    for (int i = c.lane; i < (int)(sizeof(Item) / 4); i += 32) dst[i] = from[i];
+    __syncwarp();
+    if (batch && c.lane == 0) {
+        Item *it = (Item *)c.sm;
+        it->llr = K.llr_pool + it->llr_off;
+        it->info_out = K.info_pool + it->info_off;
+        it->status_out = K.status_pool + it->status_off;
+        it->pm_out = nullptr;
+    }
+    __syncwarp();
+    const Item &it = *c.P;
+    if (c.lane < 3 * kMaxLayers) {
+        // lanes 0..11 LLR layers, 12..23 BL, 24..31 BR (and 32..35 below)
+        const int kind = c.lane / kMaxLayers, d = c.lane - kind * kMaxLayers;
+        const uint32_t mask = kind == 0 ? it.lay.llr_smem : (kind == 1 ? it.lay.bl_smem : it.lay.br_smem);
+        const uint32_t off = kind == 0 ? it.lay.llr_off[d] : (kind == 1 ? it.lay.bl_off[d] : it.lay.br_off[d]);
+        ptab(c)[c.lane] = (uint32_t *)((((mask >> d) & 1u) ? c.sm : c.gm) + off);
+    }
+    if (c.lane < 3 * kMaxLayers - 32) {
+        const int d = 32 - 2 * kMaxLayers + c.lane;
+        ptab(c)[32 + c.lane] = (uint32_t *)((((it.lay.br_smem >> d) & 1u) ? c.sm : c.gm) + it.lay.br_off[d]);
+    }
+    __syncwarp();
+    c.ops = it.ops;
+    c.n_ops = it.n_ops;
+    c.L = it.L;
+    c.fpw = 32 / it.L;
+    c.slot = c.lane & (it.L - 1);
+    c.seg = c.lane - c.slot;
+    c.fiw = c.lane / it.L;
+    c.N = it.code.N;
+    c.n = it.code.n;
+    c.n_active = 1;
+}
+
+// Persistent kernel: each warp decodes task after task.  With a task list
+// (uneven batches) the next task comes from a device counter, so warps that
+// drew short frames take more of them; otherwise warps stride over the
+// frames of the single item.
+template <class Qt, bool NODES>
+__global__ void __launch_bounds__(128, 4) scl_kernel(const __grid_constant__ KParams K)
 {
     extern __shared__ __align__(16) char smem[];
     Ctx c;
-    c.P = &P;
     const int warp = threadIdx.x >> 5;
     c.lane = threadIdx.x & 31;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
-    c.sm = smem + (size_t)warp * P.lay.smem_per_warp;
-    c.gm = P.gmem + (size_t)gwarp * P.lay.gmem_per_warp;
-    c.L = P.L;
-    c.fpw = 32 / P.L;
-    c.slot = c.lane & (P.L - 1);
-    c.seg = c.lane - c.slot;
-    c.fiw = c.lane / P.L;
-    c.N = P.code.N;
-    c.n = P.code.n;
-    c.n_active = 1;
-    const int count = P.frame_list ? *P.list_count : P.n_frames;
-    const int n_tasks = (count + c.fpw - 1) / c.fpw;
-    for (int task = gwarp; task < n_tasks; task += P.total_warps) decode_task<Qt>(c, task * c.fpw, count);
+    c.sm = smem + (size_t)warp * K.smem_per_warp;
+    c.gm = K.gmem + (size_t)gwarp * K.gmem_per_warp;
+    c.P = (const Item *)c.sm;
+    if (K.tasks == nullptr) {
+        load_item(c, &K.single, K, false);
+        const Item &it = *c.P;
+        const int count = it.frame_list ? *it.list_count : it.n_frames;
+        const int n_tasks = (count + c.fpw - 1) / c.fpw;
+        for (int task = gwarp; task < n_tasks; task += K.total_warps) decode_task<Qt, NODES>(c, task * c.fpw, count);
+        return;
+    }
+    int cur = -1;
+    for (;;) {
+        int t = 0;
+        if (c.lane == 0) t = atomicAdd(K.task_ctr, 1);
+        t = __shfl_sync(PSCL_FULL, t, 0);
+        if (t >= K.n_tasks) break;
+        const int2 tk = K.tasks[t];
+        if (tk.x != cur) {
+            load_item(c, K.items + tk.x, K, true);
+            cur = tk.x;
+        }
+        decode_task<Qt, NODES>(c, tk.y, c.P->n_frames);
+    }
 }
 
 }  // namespace pscl

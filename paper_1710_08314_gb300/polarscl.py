@@ -29,6 +29,12 @@ def pruning(mask=0, rep_max=0, spc_max=4, r1_t=2, spc_t=4, r1_max=0) -> pscl_pru
     return pscl_pruning(mask, rep_max, spc_max, r1_t, spc_t, r1_max)
 
 
+class pscl_work_item(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("n_frames", C.c_int), ("L", C.c_int), ("algo", C.c_int),
+                ("quant", C.c_int), ("pruning", C.c_void_p), ("llr_offset", C.c_size_t),
+                ("info_offset", C.c_size_t), ("status_offset", C.c_size_t)]
+
+
 class PsclError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"polarscl error {code}: {msg}")
@@ -61,6 +67,11 @@ def lib() -> C.CDLL:
             L.pscl_decode_ws.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp, C.c_size_t, vp]
             L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
             L.pscl_decode_static.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
+            L.pscl_batch_create.argtypes = [vp, i, C.POINTER(vp)]
+            L.pscl_batch_destroy.argtypes = [vp]
+            L.pscl_batch_run.argtypes = [vp, vp, vp, vp, vp]
+            L.pscl_batch_run_plain.argtypes = [vp, vp, vp, vp, vp]
+            L.pscl_batch_info.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_size_t)]
             L.pscl_last_error.restype = C.c_char_p
             L.pscl_version.restype = C.c_char_p
             L.pscl_debug_error_word.argtypes = [C.POINTER(u32)]
@@ -224,3 +235,81 @@ class Code:
         x = torch.empty((n, self.N), dtype=torch.uint8, device=info_packed.device)
         pscl_encode(self.handle, info_packed, n, x, stream)
         return x
+
+
+def pscl_batch_create(items):
+    arr = (pscl_work_item * len(items))(*items)
+    h = C.c_void_p()
+    _check(lib().pscl_batch_create(C.cast(arr, C.c_void_p), len(items), C.byref(h)))
+    return h
+
+
+def pscl_batch_destroy(batch):
+    return _check(lib().pscl_batch_destroy(batch))
+
+
+def pscl_batch_run(batch, llr_pool, info_pool, status_pool, stream=None):
+    return _check(lib().pscl_batch_run(batch, _ptr(llr_pool), _ptr(info_pool), _ptr(status_pool), _stream(stream)))
+
+
+def pscl_batch_run_plain(batch, llr_pool, info_pool, status_pool, stream=None):
+    return _check(lib().pscl_batch_run_plain(batch, _ptr(llr_pool), _ptr(info_pool), _ptr(status_pool),
+                                             _stream(stream)))
+
+
+def pscl_batch_info(batch):
+    a, b, c = C.c_int(), C.c_int(), C.c_size_t()
+    _check(lib().pscl_batch_info(batch, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+class Batch:
+    """An uneven batch over torch pools.  parts: list of dicts with keys code
+    (Code), llr (cuda float32 tensor, frames x (N-P)), L, algo, quant, prune."""
+
+    def __init__(self, parts):
+        import torch
+        self.parts = parts
+        dev = parts[0]["llr"].device
+        llr_off = info_off = st_off = 0
+        items, self.slices = [], []
+        self._prunes = []
+        for p in parts:
+            code = p["code"]
+            n = int(p["llr"].shape[0])
+            pr = p.get("prune")
+            self._prunes.append(pr)
+            items.append(pscl_work_item(code.handle.value, n, p["L"], p.get("algo", PSCL_CASCL),
+                                        p.get("quant", PSCL_F32), C.cast(C.pointer(pr), C.c_void_p) if pr else None,
+                                        llr_off, info_off, st_off))
+            self.slices.append((llr_off, n * (code.N - code.P), info_off, n * code.nbytes, st_off, n))
+            llr_off += n * (code.N - code.P)
+            info_off += n * code.nbytes
+            st_off += n
+        self.llr_pool = torch.cat([p["llr"].reshape(-1) for p in parts]).contiguous()
+        self.info_pool = torch.zeros(max(info_off, 1), dtype=torch.uint8, device=dev)
+        self.status_pool = torch.zeros(max(st_off, 1), dtype=torch.int32, device=dev)
+        self.handle = pscl_batch_create(items)
+        self.n_frames = st_off
+
+    def run(self, stream=None):
+        pscl_batch_run(self.handle, self.llr_pool, self.info_pool, self.status_pool, stream)
+
+    def run_plain(self, stream=None):
+        pscl_batch_run_plain(self.handle, self.llr_pool, self.info_pool, self.status_pool, stream)
+
+    def outputs(self, i):
+        lo, ln, io, inn, so, n = self.slices[i]
+        code = self.parts[i]["code"]
+        return self.info_pool[io:io + inn].reshape(n, code.nbytes), self.status_pool[so:so + n]
+
+    def close(self):
+        if self.handle is not None:
+            pscl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -167,3 +167,21 @@ def test_shared_memory_budget_gives_identical_results(wps):
         run_case("c3_1024_512_L8", 300, 2.0, 8, "cascl", "i8", "i8", 90 + wps, frames=np.arange(0, 300, 37))
     finally:
         ps.pscl_set_tuning(8)
+
+
+@pytest.mark.parametrize("quant,scale", [("i8", 400.0), ("i8", 0.25), ("i16", 0.03125), ("f32", 1.0)])
+@pytest.mark.parametrize("L", [4, 32])
+def test_metric_ties_resolve_in_candidate_order(quant, scale, L):
+    """Saturated or integer-valued LLRs make many path metrics equal; the
+    survivors must still be exactly the (PM, candidate id) smallest."""
+    d = synth.load_code("mcs_256_128")
+    code = oracle.Code(d["frozen"], d["crc_len"], d["crc_poly"], None, True)
+    rng = np.random.default_rng(L)
+    llr = (rng.integers(-3, 4, size=(160, 256)) * scale).astype(np.float32)
+    g = gpu_code(d)
+    for pk in [None, "all"]:
+        gp, op = prunes(pk if quant != "i8" else ("i8" if pk else None))
+        got = gpu_decode(g, llr, L, "cascl", quant, gp)
+        ref = oracle_decode(code, llr, L, "cascl", quant, op)
+        bad = compare(got, ref)
+        assert not bad, describe(got, ref, bad[0])
