@@ -1,0 +1,113 @@
+"""Autotuner for the decoder's two schedule knobs, measured on the GPU.
+
+For a code, list size, number format and pruning setting it times decodes of
+a sample batch over a grid of
+  - resident warps per SM (which sizes each warp's shared-memory slice: more
+    warps hide more latency, fewer keep more LLR layers on chip), and
+  - the largest unpruned subtree decoded in registers (node fusion),
+keeps the fastest, applies it to the code (pscl_code_tune) and stores it in a
+JSON cache keyed by the GPU model and a digest of the code, so later runs
+reuse it without measuring.  Results never depend on the tuning; only time.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import threading
+
+from . import polarscl as ps
+
+DEFAULT_CACHE = os.environ.get(
+    "PSCL_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json"))
+WARPS_GRID = (4, 8, 12, 16)
+FUSE_GRID = (2, 4, 8)
+_lock = threading.Lock()
+
+
+def gpu_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def code_digest(code) -> str:
+    h = hashlib.sha1()
+    h.update(bytes(code.frozen.tobytes()))
+    if code.puncture is not None:
+        h.update(bytes(code.puncture.tobytes()))
+    h.update(f"{code.crc_len}".encode())
+    return h.hexdigest()[:16]
+
+
+def cache_key(code, L, quant, prune, algo=ps.PSCL_CASCL) -> str:
+    pk = "none" if prune is None or prune.mask == 0 else (
+        f"{prune.mask}-{prune.rep_max}-{prune.spc_max}-{prune.r1_t}-{prune.spc_t}-{prune.r1_max}")
+    return f"{gpu_name()}|N{code.N}|K{code.K}|P{code.P}|{code_digest(code)}|L{L}|q{quant}|a{algo}|{pk}"
+
+
+def load_cache(path: str = DEFAULT_CACHE) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    os.replace(tmp, path)
+
+
+def measure(code, llr, L, quant, prune=None, algo=ps.PSCL_CASCL, warps_grid=WARPS_GRID, fuse_grid=FUSE_GRID,
+            reps=3):
+    """Time every (warps per SM, fusion) pair on the sample LLRs; returns the
+    list of results (ms per decode) and the best pair."""
+    import torch
+    n = int(llr.shape[0])
+    info = torch.empty((n, code.nbytes), dtype=torch.uint8, device=llr.device)
+    status = torch.empty((n,), dtype=torch.int32, device=llr.device)
+    results = []
+    for w in warps_grid:
+        for f in fuse_grid:
+            ps.pscl_code_tune(code.handle, L, quant, w, f)
+            ps.pscl_decode(code.handle, llr, n, L, algo, prune, quant, info, status, None, None)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ps.pscl_decode(code.handle, llr, n, L, algo, prune, quant, info, status, None, None)
+            e1.record()
+            torch.cuda.synchronize()
+            results.append(dict(warps_per_sm=w, fuse=f, ms=e0.elapsed_time(e1) / reps))
+    best = min(results, key=lambda r: r["ms"])
+    return results, best
+
+
+def tuned(code, L, quant, llr_sample=None, prune=None, algo=ps.PSCL_CASCL, path: str = DEFAULT_CACHE,
+          remeasure: bool = False):
+    """Apply cached tuning for this (code, L, format, pruning) or measure it on
+    llr_sample and cache it.  Returns the applied (warps_per_sm, fuse) and
+    whether it was measured now."""
+    key = cache_key(code, L, quant, prune, algo)
+    with _lock:
+        cache = load_cache(path)
+    hit = cache.get(key)
+    if hit and not remeasure:
+        ps.pscl_code_tune(code.handle, L, quant, hit["warps_per_sm"], hit["fuse"])
+        return (hit["warps_per_sm"], hit["fuse"]), False
+    if llr_sample is None:
+        return None, False
+    results, best = measure(code, llr_sample, L, quant, prune, algo)
+    ps.pscl_code_tune(code.handle, L, quant, best["warps_per_sm"], best["fuse"])
+    with _lock:
+        cache = load_cache(path)
+        cache[key] = dict(warps_per_sm=best["warps_per_sm"], fuse=best["fuse"], ms=best["ms"],
+                          frames=int(llr_sample.shape[0]), grid=results)
+        try:
+            save_cache(cache, path)
+        except OSError:
+            pass
+    return (best["warps_per_sm"], best["fuse"]), True

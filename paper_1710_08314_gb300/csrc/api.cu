@@ -92,6 +92,8 @@ struct pscl_code_s {
     void *d_blob = nullptr;
     std::mutex mu;
     std::map<std::vector<int>, Program> programs;
+    // measured tuning per (list size, number format): warps per SM, fusion size
+    std::map<int, std::pair<int, int>> tune;
 };
 
 static uint32_t crc_poly32(int c, uint32_t poly)
@@ -225,8 +227,24 @@ static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
     return 0;
 }
 
-// largest subtree decoded in registers (2, 4 or 8 leaves; 1 = none)
+// defaults of the two tuning knobs: the largest subtree decoded in registers
+// (2, 4 or 8 leaves; 1 = none) and the resident warps per SM the per-warp
+// shared-memory slice is sized for; per code and (L, format) the autotuner's
+// measurements override them (pscl_code_tune)
 static int g_fuse_max = 8;
+static int g_target_warps_per_sm = 16;
+
+static void tuning_for(pscl_code c, int L, int quant, int *wps, int *fuse)
+{
+    *wps = g_target_warps_per_sm;
+    *fuse = g_fuse_max;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->tune.find(L * 8 + quant);
+    if (it != c->tune.end()) {
+        *wps = it->second.first;
+        *fuse = it->second.second;
+    }
+}
 
 // true when no node of the subtree of S leaves at o is a pruned node
 static bool subtree_unpruned(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
@@ -236,7 +254,7 @@ static bool subtree_unpruned(const pscl_code_s *c, const pscl_pruning *pr, int o
     return subtree_unpruned(c, pr, o, S / 2) && subtree_unpruned(c, pr, o + S / 2, S / 2);
 }
 
-static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int o, int S, int side,
+static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, int d, int o, int S, int side,
                        std::vector<uint32_t> &ops, int &max_depth)
 {
     int type = classify(c, pr, o, S);
@@ -254,7 +272,7 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int 
         if (d > max_depth) max_depth = d;
         return PSCL_OK;
     }
-    if (d >= 1 && S <= g_fuse_max && subtree_unpruned(c, pr, o, S)) {
+    if (d >= 1 && S <= fuse && subtree_unpruned(c, pr, o, S)) {
         // the whole subtree is decoded in registers by one step
         uint32_t fz = 0;
         for (int i = 0; i < S; i++) fz |= (uint32_t)c->frozen[o + i] << i;
@@ -263,19 +281,19 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int 
         return PSCL_OK;
     }
     ops.push_back(op_make(OP_F, (uint32_t)d, 0, 0, 0));
-    int rc = gen_program(c, pr, d + 1, o, S / 2, 0, ops, max_depth);
+    int rc = gen_program(c, pr, fuse, d + 1, o, S / 2, 0, ops, max_depth);
     if (rc) return rc;
     ops.push_back(op_make(OP_G, (uint32_t)d, 0, 0, 0));
-    rc = gen_program(c, pr, d + 1, o + S / 2, S / 2, 1, ops, max_depth);
+    rc = gen_program(c, pr, fuse, d + 1, o + S / 2, S / 2, 1, ops, max_depth);
     if (rc) return rc;
     if (d > 0) ops.push_back(op_make(OP_COMB, (uint32_t)(d + 1), 0, (uint32_t)side, 0));
     return PSCL_OK;
 }
 
-static std::vector<int> prune_key(const pscl_pruning *pr)
+static std::vector<int> prune_key(const pscl_pruning *pr, int fuse)
 {
-    if (!pr || pr->mask == 0) return {g_fuse_max, 0};
-    return {g_fuse_max, (int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
+    if (!pr || pr->mask == 0) return {fuse, 0};
+    return {fuse, (int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
 }
 
 static int check_pruning(const pscl_pruning *pr)
@@ -291,12 +309,12 @@ static int check_pruning(const pscl_pruning *pr)
     return PSCL_OK;
 }
 
-static int get_program(pscl_code c, const pscl_pruning *pr, Program *out)
+static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, Program *out)
 {
     int rc = check_pruning(pr);
     if (rc) return rc;
     const pscl_pruning *eff = (pr && pr->mask) ? pr : nullptr;
-    std::vector<int> key = prune_key(pr);
+    std::vector<int> key = prune_key(pr, fuse);
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->programs.find(key);
     if (it != c->programs.end()) {
@@ -305,7 +323,7 @@ static int get_program(pscl_code c, const pscl_pruning *pr, Program *out)
     }
     std::vector<uint32_t> ops;
     int max_depth = 0;
-    rc = gen_program(c, eff, 0, 0, c->N, 1, ops, max_depth);
+    rc = gen_program(c, eff, fuse, 0, 0, c->N, 1, ops, max_depth);
     if (rc) return rc;
     Program p;
     p.n_ops = (int)ops.size();
@@ -325,11 +343,11 @@ static int get_program(pscl_code c, const pscl_pruning *pr, Program *out)
 }
 
 // lookup of an already prepared schedule; never builds or allocates
-static int find_program(pscl_code c, const pscl_pruning *pr, Program *out)
+static int find_program(pscl_code c, const pscl_pruning *pr, int fuse, Program *out)
 {
     int rc = check_pruning(pr);
     if (rc) return rc;
-    std::vector<int> key = prune_key(pr);
+    std::vector<int> key = prune_key(pr, fuse);
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->programs.find(key);
     if (it == c->programs.end())
@@ -341,8 +359,35 @@ static int find_program(pscl_code c, const pscl_pruning *pr, Program *out)
 extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
-    Program p;
-    return get_program(c, pr, &p);
+    // the default schedule and every fusion size the code's tuning uses
+    std::vector<int> fuses = {g_fuse_max};
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (auto &kv : c->tune) fuses.push_back(kv.second.second);
+    }
+    for (int f : fuses) {
+        Program p;
+        int rc = get_program(c, pr, f, &p);
+        if (rc) return rc;
+    }
+    return PSCL_OK;
+}
+
+extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, int warps_per_sm, int fuse_leaves)
+{
+    if (!c) return fail(PSCL_EINVAL, "code is NULL");
+    if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return fail(PSCL_EINVAL, "L=%d", L);
+    if (quant < PSCL_F32 || quant > PSCL_I8) return fail(PSCL_EINVAL, "unknown quantisation %d", (int)quant);
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (warps_per_sm == 0 && fuse_leaves == 0) {
+        c->tune.erase(L * 8 + (int)quant);
+        return PSCL_OK;
+    }
+    if (warps_per_sm < 1 || warps_per_sm > 32) return fail(PSCL_EINVAL, "warps per SM %d out of 1..32", warps_per_sm);
+    if (fuse_leaves != 1 && fuse_leaves != 2 && fuse_leaves != 4 && fuse_leaves != 8)
+        return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8", fuse_leaves);
+    c->tune[L * 8 + (int)quant] = std::make_pair(warps_per_sm, fuse_leaves);
+    return PSCL_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -425,11 +470,10 @@ struct Plan {
     size_t total_ws = 0;
     int n_stages = 0;
     int stages[8];
+    size_t budget = 0;         // shared-memory bytes per warp
 };
 
 static const int kWarpsPerBlock = 4;
-// target resident warps per SM; each warp's shared slice is sized to fit
-static int g_target_warps_per_sm = 16;
 
 static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const pscl_pruning *pr, pscl_quant quant,
                      Plan *pl, bool build_program = true)
@@ -443,7 +487,9 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     int dev;
     CU(cudaGetDevice(&dev));
     if (dev != c->dev) return fail(PSCL_EINVAL, "code was created on device %d, current device is %d", c->dev, dev);
-    int rc = build_program ? get_program(c, pr, &pl->pg) : find_program(c, pr, &pl->pg);
+    int wps, fuse;
+    tuning_for(c, L, (int)quant, &wps, &fuse);
+    int rc = build_program ? get_program(c, pr, fuse, &pl->pg) : find_program(c, pr, fuse, &pl->pg);
     if (rc) return rc;
     DevProps dp;
     rc = get_props(&dp);
@@ -464,8 +510,9 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     // list size needs the most layer-0 room, the largest the most paths:
     // both only depend on N, EPW and 32/L for layer 0)
     const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
-    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
+    size_t budget = per_sm / (size_t)wps;
     if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    pl->budget = budget;
     // each stage recomputes its own layout at launch; the plan keeps maxima
     uint32_t max_smem = 0, max_gmem = 0;
     for (int s = 0; s < pl->n_stages; s++) {
@@ -530,12 +577,7 @@ static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_a
     int32_t *counts = (int32_t *)(w + 64);  // two list counters
     int32_t *lists = (int32_t *)(w + 256);
     char *gmem = w + 256 + pl.list_bytes;
-    DevProps dp;
-    int rc = get_props(&dp);
-    if (rc) return rc;
-    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
-    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
-    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    const size_t budget = pl.budget;
     int launches = 0;
     for (int s = 0; s < pl.n_stages; s++) {
         const int Ls = pl.stages[s];
@@ -817,7 +859,9 @@ extern "C" int pscl_batch_create(const pscl_work_item *items, int n_items, pscl_
             batch_free(b);
             return fail(PSCL_EINVAL, "item %d: bad quantisation or frame count", i);
         }
-        rc = get_program(w.code, w.pruning, &progs[(size_t)i]);
+        int wps_i, fuse_i;
+        tuning_for(w.code, w.algo == PSCL_SC ? 1 : w.L, (int)w.quant, &wps_i, &fuse_i);
+        rc = get_program(w.code, w.pruning, fuse_i, &progs[(size_t)i]);
         if (rc) { batch_free(b); return rc; }
     }
     void *p;

@@ -67,6 +67,7 @@ def lib() -> C.CDLL:
             L.pscl_decode_ws.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp, C.c_size_t, vp]
             L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
             L.pscl_decode_static.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
+            L.pscl_code_tune.argtypes = [vp, i, i, i, i]
             L.pscl_batch_create.argtypes = [vp, i, C.POINTER(vp)]
             L.pscl_batch_destroy.argtypes = [vp]
             L.pscl_batch_run.argtypes = [vp, vp, vp, vp, vp]
@@ -139,6 +140,10 @@ def pscl_code_info(code):
     return N.value, K.value, Ki.value, P.value
 
 
+def pscl_code_tune(code, L, quant, warps_per_sm, fuse_leaves):
+    return _check(lib().pscl_code_tune(code, L, quant, warps_per_sm, fuse_leaves))
+
+
 def pscl_prepare(code, prune=None):
     return _check(lib().pscl_prepare(code, C.byref(prune) if prune is not None else None))
 
@@ -201,6 +206,8 @@ class Code:
     def __init__(self, frozen, crc_len=0, crc_poly=0, puncture=None, systematic=True):
         import numpy as np
         fr = np.asarray(frozen, dtype=np.uint8)
+        self.frozen = fr.copy()
+        self.puncture = None if puncture is None else np.asarray(puncture, dtype=np.uint8).copy()
         self.N = int(fr.size)
         self.K = int(self.N - (fr != 0).sum())
         self.crc_len = int(crc_len)

@@ -1,0 +1,30 @@
+"""The autotuner measures schedule knobs; whatever it picks, results stay
+bit-exact, and its cache round-trips."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import gpu_code, make_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_picks_applies_and_caches(tmp_path):
+    import torch
+    from paper_1710_08314_gb300 import autotune, polarscl as ps
+    d = synth.load_code("c3_1024_512_L8")
+    g = gpu_code(d)
+    _, _, llr = make_inputs(d, 512, 2.0, 3)
+    t = torch.from_numpy(llr).cuda()
+    ref_info, ref_st, _ = g.decode(t, 8, ps.PSCL_CASCL, None, ps.PSCL_I16)
+    path = str(tmp_path / "tune.json")
+    (w, f), measured = autotune.tuned(g, 8, ps.PSCL_I16, t, path=path)
+    assert measured and w in autotune.WARPS_GRID and f in autotune.FUSE_GRID
+    info, st, _ = g.decode(t, 8, ps.PSCL_CASCL, None, ps.PSCL_I16)
+    assert torch.equal(info, ref_info) and torch.equal(st, ref_st)
+    g2 = gpu_code(d)
+    (w2, f2), measured2 = autotune.tuned(g2, 8, ps.PSCL_I16, None, path=path)
+    assert not measured2 and (w2, f2) == (w, f)
+    assert os.path.exists(path)
