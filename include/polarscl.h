@@ -211,6 +211,75 @@ int pscl_batch_run_plain(pscl_batch batch, const float *llr_pool, uint8_t *info_
 /* Launches per run, total tasks and scratch bytes of a plan.                */
 int pscl_batch_info(pscl_batch batch, int *n_launches, int *n_tasks, size_t *scratch_bytes);
 
+/* ---------------------------------------------------------------------------
+ * Serving loop: a device-resident request loop with continuous batching.
+ * The server keeps its decoding contexts (code, list size, pruning; one
+ * number format per server) and all frame state on the GPU and runs one
+ * persistent kernel on its own stream.  Requests are published through a
+ * ring in mapped host memory; the kernel's warps take 32/L-frame tasks from
+ * every open request, so requests that arrive while others decode share the
+ * GPU with them at once.  Results equal pscl_decode's (CASCL, or SC for
+ * L = 1) frame by frame.  Every device-side wait is bounded: after
+ * idle_timeout_ms without any new request the kernel exits by itself and
+ * pscl_server_status reports PSCL_ETIMEDOUT; pscl_server_stop raises an
+ * abort word that the warps check between tasks.  While a server runs, wait
+ * on streams or events only: a device-wide synchronisation waits for the
+ * serving kernel itself, which ends only on stop or its idle budget.        */
+typedef struct pscl_server_s *pscl_server;
+
+typedef struct {
+    pscl_code code;
+    int L;
+    const pscl_pruning *pruning;  /* NULL = none (read at start only) */
+} pscl_context;
+
+typedef struct {
+    const pscl_context *contexts;
+    int n_contexts;
+    pscl_quant quant;
+    int ring_slots;               /* requests in flight at most, power of two */
+    int max_frames_per_request;
+    long long max_inflight_frames;/* admission budget (frames); 0 = ring x max */
+    int idle_timeout_ms;          /* device loop exits after this long idle */
+    int max_warps;                /* 0 = every resident warp */
+} pscl_server_cfg;
+
+/* A request: context index, frame count and DEVICE buffers whose contents
+ * are ready when pscl_server_submit is called (llr: n_frames x (N - P)
+ * floats; info_out: n_frames x ceil(K_info/8) bytes; status_out: int32 per
+ * frame, as in pscl_decode).                                               */
+typedef struct {
+    int context;
+    int n_frames;
+    const float *llr;
+    uint8_t *info_out;
+    int32_t *status_out;
+} pscl_request;
+
+typedef struct {
+    uint64_t ticket;
+    int status;                   /* 0 = decoded */
+    int n_frames;
+    uint64_t t_submit_ns;         /* host CLOCK_MONOTONIC at submit */
+    uint64_t t_done_ns;           /* host CLOCK_MONOTONIC when polled complete */
+    uint64_t device_ns;           /* device time from opening to last frame */
+} pscl_completion;
+
+/* Allocates the server's device and mapped memory and launches its kernel. */
+int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out);
+/* Thread-safe, non-blocking.  PSCL_EAGAIN when the ring or the frame budget
+ * is full (nothing is dropped; retry), PSCL_EINVAL for a malformed request. */
+int pscl_server_submit(pscl_server s, const pscl_request *req, uint64_t *ticket);
+/* Collect up to max completed requests (non-blocking).                     */
+int pscl_server_poll(pscl_server s, pscl_completion *out, int max, int *n_out);
+/* running: kernel still resident; device_status: PSCL_ETIMEDOUT once it left
+ * on its idle budget.                                                       */
+int pscl_server_status(pscl_server s, int *running, int *device_status, uint64_t *completed,
+                       long long *frames_in_flight);
+/* Raise the abort word and wait (at most timeout_ms) for the kernel to end,
+ * then free everything; PSCL_ETIMEDOUT keeps the resources.                 */
+int pscl_server_stop(pscl_server s, int timeout_ms);
+
 /* Message for the calling thread's most recent error ("" if none).         */
 const char *pscl_last_error(void);
 

@@ -8,8 +8,10 @@
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
+#include <time.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -1044,5 +1046,269 @@ extern "C" int pscl_batch_info(pscl_batch b, int *n_launches, int *n_tasks, size
     if (n_launches) *n_launches = (int)b->groups.size();
     if (n_tasks) *n_tasks = t;
     if (scratch_bytes) *scratch_bytes = bytes;
+    return PSCL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving loop: host side (device side in server.cu).
+static uint64_t host_ns()
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+struct pscl_server_s {
+    int dev = -1;
+    int quant = 0;
+    bool nodes = false;
+    int R = 0;
+    int max_frames = 0;
+    long long max_inflight = 0;
+    int grid = 0, total_warps = 0;
+    size_t smem_block = 0;
+    std::vector<Item> h_items;
+    std::vector<pscl_code> codes;
+    Item *d_items = nullptr;
+    SrvCtl *ctl = nullptr;      // mapped host memory (host view)
+    SrvReq *ring = nullptr;
+    SrvComp *comp = nullptr;
+    char *d_mem = nullptr;      // device: counters, requests, claims, scratch
+    cudaStream_t stream = nullptr;
+    bool running = false;
+    std::mutex mu;
+    uint64_t next_ticket = 0;
+    std::vector<uint64_t> slot_ticket;
+    std::vector<char> slot_busy;
+    std::vector<uint64_t> slot_submit_ns;
+    std::vector<int> slot_frames;
+    long long inflight = 0;
+    uint64_t completed = 0;
+};
+
+static void server_free(pscl_server s)
+{
+    if (s->d_items) cudaFree(s->d_items);
+    if (s->d_mem) cudaFree(s->d_mem);
+    if (s->ctl) cudaFreeHost(s->ctl);
+    if (s->ring) cudaFreeHost(s->ring);
+    if (s->comp) cudaFreeHost(s->comp);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
+{
+    if (!cfg || !out) return fail(PSCL_EINVAL, "cfg and out are required");
+    *out = nullptr;
+    const int R = cfg->ring_slots;
+    if (R < 2 || R > 65536 || (R & (R - 1))) return fail(PSCL_EINVAL, "ring_slots=%d: a power of two in [2, 65536]", R);
+    if (cfg->n_contexts < 1 || !cfg->contexts) return fail(PSCL_EINVAL, "no decoding contexts");
+    if (cfg->max_frames_per_request < 1) return fail(PSCL_EINVAL, "max_frames_per_request < 1");
+    if (cfg->quant < PSCL_F32 || cfg->quant > PSCL_I8) return fail(PSCL_EINVAL, "unknown quantisation");
+    if (cfg->idle_timeout_ms < 1) return fail(PSCL_EINVAL, "idle_timeout_ms < 1");
+    DevProps dp;
+    int rc = get_props(&dp);
+    if (rc) return rc;
+    pscl_server s = new pscl_server_s();
+    CU(cudaGetDevice(&s->dev));
+    s->quant = (int)cfg->quant;
+    s->R = R;
+    s->max_frames = cfg->max_frames_per_request;
+    s->max_inflight = cfg->max_inflight_frames > 0 ? cfg->max_inflight_frames : (long long)R * cfg->max_frames_per_request;
+    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
+    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
+    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    uint32_t smem_pw = 0, gmem_pw = 0;
+    s->h_items.resize((size_t)cfg->n_contexts);
+    for (int i = 0; i < cfg->n_contexts; i++) {
+        const pscl_context &cx = cfg->contexts[i];
+        if (!cx.code || cx.code->dev != s->dev) { server_free(s); return fail(PSCL_EINVAL, "context %d: bad code", i); }
+        if (cx.L != 1 && cx.L != 2 && cx.L != 4 && cx.L != 8 && cx.L != 16 && cx.L != 32) {
+            server_free(s);
+            return fail(PSCL_EINVAL, "context %d: L=%d", i, cx.L);
+        }
+        int wps, fuse;
+        tuning_for(cx.code, cx.L, s->quant, &wps, &fuse);
+        Program pg;
+        rc = get_program(cx.code, cx.pruning, fuse, &pg);
+        if (rc) { server_free(s); return rc; }
+        if (pg.has_nodes) s->nodes = true;
+        Item &it = s->h_items[(size_t)i];
+        memset(&it, 0, sizeof(it));
+        it.code = cx.code->dc;
+        it.ops = pg.d_ops;
+        it.n_ops = pg.n_ops;
+        it.root_special = pg.root_special;
+        make_layout(cx.code, pg, cx.L, s->quant, budget, &it.lay);
+        it.L = cx.L;
+        it.L_out = cx.L;
+        it.stage_L = cx.L;
+        if (it.lay.smem_per_warp > smem_pw) smem_pw = it.lay.smem_per_warp;
+        if (it.lay.gmem_per_warp > gmem_pw) gmem_pw = it.lay.gmem_per_warp;
+        s->codes.push_back(cx.code);
+    }
+    s->smem_block = (size_t)smem_pw * kWarpsPerBlock;
+    int bps = 0;
+    cudaError_t e = server_attrs(s->quant, s->nodes, s->smem_block, &bps);
+    if (e != cudaSuccess || bps < 1) {
+        server_free(s);
+        return fail(PSCL_EUNSUPPORTED, "server: no block fits (%zu bytes of shared memory)", s->smem_block);
+    }
+    int warps = dp.sms * bps * kWarpsPerBlock;
+    if (cfg->max_warps > 0 && cfg->max_warps < warps) warps = cfg->max_warps / kWarpsPerBlock * kWarpsPerBlock;
+    if (warps < kWarpsPerBlock) warps = kWarpsPerBlock;
+    s->grid = warps / kWarpsPerBlock;
+    s->total_warps = s->grid * kWarpsPerBlock;
+    // device memory: counters | open requests | claims | done | scratch
+    const size_t off_dreq = 256, off_claim = off_dreq + sizeof(SrvDReq) * (size_t)R,
+                 off_done = off_claim + 8 * (size_t)R, off_gmem = (off_done + 4 * (size_t)R + 255) & ~(size_t)255,
+                 total = off_gmem + (size_t)gmem_pw * (size_t)s->total_warps;
+    e = cudaMalloc(&s->d_mem, total);
+    if (e == cudaSuccess) e = cudaMemset(s->d_mem, 0, off_gmem);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_items, sizeof(Item) * s->h_items.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_items, s->h_items.data(), sizeof(Item) * s->h_items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->ctl, sizeof(SrvCtl), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->ring, sizeof(SrvReq) * (size_t)R, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->comp, sizeof(SrvComp) * (size_t)R, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        server_free(s);
+        return fail(e == cudaErrorMemoryAllocation ? PSCL_ENOMEM : PSCL_ECUDA, "server: %s", cudaGetErrorString(e));
+    }
+    memset(s->ctl, 0, sizeof(SrvCtl));
+    memset(s->ring, 0, sizeof(SrvReq) * (size_t)R);
+    memset(s->comp, 0, sizeof(SrvComp) * (size_t)R);
+    s->slot_ticket.assign((size_t)R, 0);
+    s->slot_busy.assign((size_t)R, 0);
+    s->slot_submit_ns.assign((size_t)R, 0);
+    s->slot_frames.assign((size_t)R, 0);
+    SrvParams P;
+    memset(&P, 0, sizeof(P));
+    P.K.items = s->d_items;
+    P.K.gmem = s->d_mem + off_gmem;
+    P.K.gmem_per_warp = gmem_pw;
+    P.K.smem_per_warp = smem_pw;
+    P.K.total_warps = s->total_warps;
+    P.n_ctx = cfg->n_contexts;
+    void *dp_ctl, *dp_ring, *dp_comp;
+    cudaHostGetDevicePointer(&dp_ctl, s->ctl, 0);
+    cudaHostGetDevicePointer(&dp_ring, s->ring, 0);
+    cudaHostGetDevicePointer(&dp_comp, s->comp, 0);
+    P.ctl = (SrvCtl *)dp_ctl;
+    P.ring = (SrvReq *)dp_ring;
+    P.comp = (SrvComp *)dp_comp;
+    P.dev = (SrvDev *)s->d_mem;
+    P.dreq = (SrvDReq *)(s->d_mem + off_dreq);
+    P.claim = (unsigned long long *)(s->d_mem + off_claim);
+    P.done = (uint32_t *)(s->d_mem + off_done);
+    P.R = R;
+    P.idle_ns = (unsigned long long)cfg->idle_timeout_ms * 1000000ull;
+    e = server_launch(s->quant, s->nodes, P, s->grid, s->smem_block, s->stream);
+    if (e != cudaSuccess) {
+        server_free(s);
+        return fail(PSCL_ECUDA, "server launch: %s", cudaGetErrorString(e));
+    }
+    s->running = true;
+    *out = s;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_server_submit(pscl_server s, const pscl_request *req, uint64_t *ticket)
+{
+    if (!s || !req) return fail(PSCL_EINVAL, "server and request are required");
+    if (req->context < 0 || req->context >= (int)s->h_items.size())
+        return fail(PSCL_EINVAL, "request context %d out of range", req->context);
+    if (req->n_frames < 1 || req->n_frames > s->max_frames)
+        return fail(PSCL_EINVAL, "request of %d frames (1..%d)", req->n_frames, s->max_frames);
+    if (!req->llr || !req->info_out || !req->status_out) return fail(PSCL_EINVAL, "request buffers are required");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->running) return fail(PSCL_EINVAL, "server is stopped");
+    const uint64_t t = s->next_ticket;
+    const int slot = (int)(t & (uint64_t)(s->R - 1));
+    if (s->slot_busy[(size_t)slot] || s->inflight + req->n_frames > s->max_inflight)
+        return fail(PSCL_EAGAIN, "server full: %lld frames in flight", s->inflight);
+    SrvReq &r = s->ring[slot];
+    r.ctx = req->context;
+    r.n = req->n_frames;
+    r.llr = req->llr;
+    r.info = req->info_out;
+    r.status = req->status_out;
+    s->slot_ticket[(size_t)slot] = t;
+    s->slot_busy[(size_t)slot] = 1;
+    s->slot_submit_ns[(size_t)slot] = host_ns();
+    s->slot_frames[(size_t)slot] = req->n_frames;
+    s->inflight += req->n_frames;
+    s->next_ticket = t + 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *(volatile uint32_t *)&s->ctl->tail = (uint32_t)(t + 1);
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    if (ticket) *ticket = t;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_server_poll(pscl_server s, pscl_completion *out, int max, int *n_out)
+{
+    if (!s || !n_out || (max > 0 && !out)) return fail(PSCL_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(s->mu);
+    int n = 0;
+    for (int slot = 0; slot < s->R && n < max; slot++) {
+        if (!s->slot_busy[(size_t)slot]) continue;
+        volatile SrvComp *c = s->comp + slot;
+        const uint64_t t = s->slot_ticket[(size_t)slot];
+        if (c->seq != (uint32_t)(t + 1)) continue;
+        std::atomic_thread_fence(std::memory_order_acquire);
+        pscl_completion &o = out[n++];
+        o.ticket = t;
+        o.status = c->status;
+        o.n_frames = s->slot_frames[(size_t)slot];
+        o.t_submit_ns = s->slot_submit_ns[(size_t)slot];
+        o.t_done_ns = host_ns();
+        o.device_ns = c->t_end - c->t_open;
+        s->slot_busy[(size_t)slot] = 0;
+        s->inflight -= o.n_frames;
+        s->completed++;
+    }
+    *n_out = n;
+    if (s->running && s->ctl->exit_status == PSCL_ETIMEDOUT && cudaStreamQuery(s->stream) == cudaSuccess)
+        s->running = false;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_server_status(pscl_server s, int *running, int *device_status, uint64_t *completed,
+                                  long long *frames_in_flight)
+{
+    if (!s) return fail(PSCL_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const bool alive = cudaStreamQuery(s->stream) == cudaErrorNotReady;
+    if (running) *running = alive ? 1 : 0;
+    if (device_status) *device_status = s->ctl->exit_status;
+    if (completed) *completed = s->completed;
+    if (frames_in_flight) *frames_in_flight = s->inflight;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_server_stop(pscl_server s, int timeout_ms)
+{
+    if (!s) return fail(PSCL_EINVAL, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->running = false;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        *(volatile uint32_t *)&s->ctl->abort = 1u;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+    }
+    const uint64_t t0 = host_ns();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(s->stream);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return fail(PSCL_ECUDA, "server stream: %s", cudaGetErrorString(q));
+        if (host_ns() - t0 > (uint64_t)timeout_ms * 1000000ull)
+            return fail(PSCL_ETIMEDOUT, "the serving loop did not stop within %d ms (resources kept)", timeout_ms);
+        struct timespec ts = {0, 200000};
+        nanosleep(&ts, nullptr);
+    }
+    server_free(s);
     return PSCL_OK;
 }

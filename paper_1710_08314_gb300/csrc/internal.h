@@ -115,6 +115,57 @@ cudaError_t launch_scl_i16(const KParams &p, bool nodes, int grid, int block, si
 cudaError_t launch_scl_i8(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t scl_func_attrs(int quant, bool nodes, size_t smem, int block, int *blocks_per_sm);
 
+// ---------------------------------------------------------------------------
+// serving loop (server.cu)
+struct SrvReq {            // ring entry, written by the host
+    int ctx;
+    int n;
+    const float *llr;
+    uint8_t *info;
+    int32_t *status;
+};
+struct SrvComp {           // completion record, written by the device
+    unsigned long long t_open, t_end;
+    int status;
+    uint32_t seq;          // ticket + 1 once complete
+};
+struct SrvCtl {            // control block in mapped memory
+    uint32_t tail;         // tickets published by the host
+    uint32_t abort;        // host sets 1 to stop the loop
+    int32_t exit_status;   // device: PSCL_ETIMEDOUT when it left on its idle budget
+    uint32_t pad;
+};
+struct SrvDReq {           // device copy of an open request
+    int ctx, n;
+    const float *llr;
+    uint8_t *info;
+    int32_t *status;
+    unsigned long long t_open;
+};
+struct SrvDev {            // device-side counters
+    uint32_t opened;       // tickets copied into device memory
+    uint32_t opening;      // ticket range being copied (CAS guard)
+    uint32_t head;         // oldest ticket that may still have unclaimed frames
+    uint32_t abort;        // device copy of the abort word
+};
+
+struct SrvParams {
+    KParams K;             // items, gmem, gmem_per_warp, smem_per_warp, total_warps
+    int n_ctx;
+    SrvCtl *ctl;
+    SrvReq *ring;
+    SrvComp *comp;
+    SrvDev *dev;
+    SrvDReq *dreq;
+    unsigned long long *claim;   // ticket << 32 | next frame
+    uint32_t *done;              // frames finished
+    int R;                       // ring slots (power of two)
+    unsigned long long idle_ns;
+};
+
+cudaError_t server_attrs(int quant, bool nodes, size_t smem, int *blocks_per_sm);
+cudaError_t server_launch(int quant, bool nodes, const SrvParams &S, int grid, size_t smem, cudaStream_t s);
+
 struct EncParams {
     DevCode code;
     const uint8_t *info;

@@ -35,6 +35,26 @@ class pscl_work_item(C.Structure):
                 ("info_offset", C.c_size_t), ("status_offset", C.c_size_t)]
 
 
+class pscl_context(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("L", C.c_int), ("pruning", C.c_void_p)]
+
+
+class pscl_server_cfg(C.Structure):
+    _fields_ = [("contexts", C.c_void_p), ("n_contexts", C.c_int), ("quant", C.c_int), ("ring_slots", C.c_int),
+                ("max_frames_per_request", C.c_int), ("max_inflight_frames", C.c_longlong),
+                ("idle_timeout_ms", C.c_int), ("max_warps", C.c_int)]
+
+
+class pscl_request(C.Structure):
+    _fields_ = [("context", C.c_int), ("n_frames", C.c_int), ("llr", C.c_void_p), ("info_out", C.c_void_p),
+                ("status_out", C.c_void_p)]
+
+
+class pscl_completion(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("status", C.c_int), ("n_frames", C.c_int), ("t_submit_ns", C.c_uint64),
+                ("t_done_ns", C.c_uint64), ("device_ns", C.c_uint64)]
+
+
 class PsclError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"polarscl error {code}: {msg}")
@@ -68,6 +88,12 @@ def lib() -> C.CDLL:
             L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
             L.pscl_decode_static.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
             L.pscl_code_tune.argtypes = [vp, i, i, i, i]
+            L.pscl_server_start.argtypes = [vp, C.POINTER(vp)]
+            L.pscl_server_submit.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
+            L.pscl_server_poll.argtypes = [vp, vp, i, C.POINTER(i)]
+            L.pscl_server_status.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_uint64),
+                                             C.POINTER(C.c_longlong)]
+            L.pscl_server_stop.argtypes = [vp, i]
             L.pscl_batch_create.argtypes = [vp, i, C.POINTER(vp)]
             L.pscl_batch_destroy.argtypes = [vp]
             L.pscl_batch_run.argtypes = [vp, vp, vp, vp, vp]
@@ -320,3 +346,68 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def pscl_server_start(cfg):
+    h = C.c_void_p()
+    _check(lib().pscl_server_start(C.byref(cfg), C.byref(h)))
+    return h
+
+
+def pscl_server_submit(server, req):
+    """Returns the ticket, or None when the server is full (PSCL_EAGAIN)."""
+    t = C.c_uint64()
+    rc = lib().pscl_server_submit(server, C.byref(req), C.byref(t))
+    if rc == PSCL_EAGAIN:
+        return None
+    _check(rc)
+    return t.value
+
+
+def pscl_server_poll(server, max_n=256):
+    arr = (pscl_completion * max_n)()
+    n = C.c_int()
+    _check(lib().pscl_server_poll(server, C.cast(arr, C.c_void_p), max_n, C.byref(n)))
+    return [arr[k] for k in range(n.value)]
+
+
+def pscl_server_status(server):
+    r, st, done, fl = C.c_int(), C.c_int(), C.c_uint64(), C.c_longlong()
+    _check(lib().pscl_server_status(server, C.byref(r), C.byref(st), C.byref(done), C.byref(fl)))
+    return dict(running=bool(r.value), device_status=st.value, completed=done.value, in_flight=fl.value)
+
+
+def pscl_server_stop(server, timeout_ms=5000):
+    return _check(lib().pscl_server_stop(server, timeout_ms))
+
+
+class Server:
+    """Serving loop over a list of (Code, L, prune) contexts."""
+
+    def __init__(self, contexts, quant=PSCL_F32, ring_slots=256, max_frames=256, max_inflight=0,
+                 idle_timeout_ms=5000, max_warps=0):
+        self._ctx_arr = (pscl_context * len(contexts))()
+        self._keep = []
+        for k, (code, L, prune) in enumerate(contexts):
+            self._ctx_arr[k].code = code.handle.value
+            self._ctx_arr[k].L = L
+            self._ctx_arr[k].pruning = C.cast(C.pointer(prune), C.c_void_p) if prune is not None else None
+            self._keep.append((code, prune))
+        self.cfg = pscl_server_cfg(C.cast(self._ctx_arr, C.c_void_p).value, len(contexts), quant, ring_slots,
+                                   max_frames, max_inflight, idle_timeout_ms, max_warps)
+        self.handle = pscl_server_start(self.cfg)
+
+    def submit(self, context, llr, info_out, status_out):
+        req = pscl_request(context, int(llr.shape[0]), llr.data_ptr(), info_out.data_ptr(), status_out.data_ptr())
+        return pscl_server_submit(self.handle, req)
+
+    def poll(self, max_n=256):
+        return pscl_server_poll(self.handle, max_n)
+
+    def status(self):
+        return pscl_server_status(self.handle)
+
+    def stop(self, timeout_ms=5000):
+        if self.handle is not None:
+            pscl_server_stop(self.handle, timeout_ms)
+            self.handle = None
