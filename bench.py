@@ -15,6 +15,8 @@ from __future__ import annotations
 import argparse
 import json
 import math
+
+import numpy as np
 import os
 import subprocess
 import sys
@@ -29,6 +31,10 @@ L_LIST = 32
 BATCH = 16384            # frames per step: 134 MB of LLRs, larger than L2
 ALGO_CASCL = 1
 QUANT = {"f32": 0, "i16": 1, "i8": 2}
+
+
+def log(msg):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 def dist_env():
@@ -164,6 +170,223 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# ---------------------------------------------------------------------------
+# Further workloads, reported beside the headline (same JSON line).
+def _gen_frames(code, n, ebn0_db, gen, sigma_per_frame=None):
+    """Synthetic frames on the device: random info bits -> library encoder ->
+    BPSK-AWGN channel.  Returns (info_packed, llr)."""
+    import torch
+    import synth
+    info = torch.randint(0, 256, (n, code.nbytes), generator=gen, device="cuda", dtype=torch.uint8)
+    if code.K_info % 8:
+        info[:, -1] &= (0xFF << (8 - code.K_info % 8)) & 0xFF
+    x = code.encode(info)
+    keep = None
+    if code.puncture is not None:
+        keep = torch.from_numpy(np.flatnonzero(code.puncture == 0)).cuda()
+    sig = sigma_per_frame if sigma_per_frame is not None else synth.sigma_for(ebn0_db, code.K_info / (code.N - code.P))
+    llr = synth.torch_bpsk_awgn_llr(x, sig, gen, keep)
+    return info, llr
+
+
+def _timed(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _code(name):
+    import synth
+    from paper_1710_08314_gb300 import Code
+    d = synth.load_code(name)
+    return d, Code(d["frozen"], d["crc_len"], d["crc_poly"], d["punct"], d["systematic"])
+
+
+def run_c1(gen):
+    """Plain CA-SCL (128, 64 incl. CRC-8), L = 4, f32, no pruning, 2.0 dB, 10,000 frames."""
+    import torch
+    from paper_1710_08314_gb300 import polarscl as ps
+    d, code = _code("c1_cascl_128_64_L4")
+    info, llr = _gen_frames(code, 10000, 2.0, gen)
+    out = torch.empty_like(info)
+    st = torch.empty((10000,), dtype=torch.int32, device="cuda")
+    ms = _timed(lambda: ps.pscl_decode(code.handle, llr, 10000, 4, 1, None, 0, out, st, None, None))
+    fer = float((out != info).any(dim=1).float().mean())
+    return dict(value=10000 * code.K_info / ms / 1e3, unit="Mb/s", ms=ms, frames=10000, fer=fer,
+                latency_ms_batch=ms)
+
+
+def run_c2(gen, snrs=(3.5, 4.0, 4.5), frames=200000):
+    """Adaptive FA-SSCL (2048, 1723 incl. CRC-32), Lmax = 32, pruned
+    (R0/R1/REP/SPC4; REP8- for int8), f32 and int8."""
+    import torch
+    from paper_1710_08314_gb300 import pruning, polarscl as ps
+    d, code = _code("c2_2048_1723")
+    out = {}
+    for quant, qn, pr in [(0, "f32", pruning(15, rep_max=0)), (2, "i8", pruning(15, rep_max=8))]:
+        for snr in snrs:
+            info, llr = _gen_frames(code, frames, snr, gen)
+            o = torch.empty_like(info)
+            st = torch.empty((frames,), dtype=torch.int32, device="cuda")
+            ms = _timed(lambda: ps.pscl_decode(code.handle, llr, frames, 32, ps.PSCL_FASCL, pr, quant, o, st,
+                                               None, None), reps=2)
+            Ls = ((st >> 8) & 0xFF).cpu().numpy()
+            hist = {str(int(L)): int((Ls == L).sum()) for L in [1, 2, 4, 8, 16, 32]}
+            out[f"{qn}_{snr}dB"] = dict(value=frames * code.K_info / ms / 1e3, unit="Mb/s", frames=frames,
+                                        fer=float((o != info).any(dim=1).float().mean()), final_L_hist=hist,
+                                        ms=ms)
+            del info, llr, o, st
+    return out
+
+
+def run_c3(gen, snr=2.0, frames=100000):
+    """CA-SCL (1024, 512 incl. CRC-16), L = 8: pruned vs unpruned, int16 and f32."""
+    import torch
+    from paper_1710_08314_gb300 import pruning, polarscl as ps
+    d, code = _code("c3_1024_512_L8")
+    info, llr = _gen_frames(code, frames, snr, gen)
+    o = torch.empty_like(info)
+    st = torch.empty((frames,), dtype=torch.int32, device="cuda")
+    out = {}
+    for qn, quant in [("f32", 0), ("i16", 1)]:
+        for pn, pr in [("unpruned", None), ("pruned", pruning(15, rep_max=0))]:
+            ms = _timed(lambda: ps.pscl_decode(code.handle, llr, frames, 8, 1, pr, quant, o, st, None, None))
+            out[f"{qn}_{pn}"] = dict(value=frames * code.K_info / ms / 1e3, unit="Mb/s", frames=frames,
+                                     fer=float((o != info).any(dim=1).float().mean()), ms=ms)
+    return out
+
+
+def run_c4(gen, total=500000, seed=7):
+    """Uneven batch: 500,000 frames over 48 code contexts (N 128..2048, rate
+    1/4..8/9, L 1..32, CRC-8/16/32, 0-20 % quasi-uniform puncturing, Eb/N0 per
+    frame uniform in 0-5 dB), f32 and int8 contexts; persistent launch vs one
+    launch per work item vs CUDA-graph replay."""
+    import torch
+    import synth
+    from paper_1710_08314_gb300 import polarscl as ps
+    from paper_1710_08314_gb300.polarscl import Batch
+    names = json.load(open(os.path.join(ROOT, "tests", "golden", "codes", "uneven_index.json")))
+    rng = np.random.default_rng(seed)
+    counts = np.bincount(rng.integers(0, len(names), total), minlength=len(names))
+    parts, refs = [], []
+    for k, name in enumerate(names):
+        d, code = _code(name)
+        n = int(counts[k])
+        ebn0 = torch.from_numpy(rng.uniform(0.0, 5.0, n)).cuda()
+        rate = code.K_info / (code.N - code.P)
+        sig = torch.sqrt(1.0 / (2.0 * rate * torch.pow(10.0, ebn0 / 10.0))).float()
+        info, llr = _gen_frames(code, n, None, gen, sigma_per_frame=sig)
+        quant = ps.PSCL_I8 if k % 2 else ps.PSCL_F32
+        parts.append(dict(code=code, llr=llr, L=d["L"], algo=ps.PSCL_CASCL, quant=quant))
+        refs.append(info)
+    b = Batch(parts)
+    n_launch, n_tasks, scratch = ps.pscl_batch_info(b.handle)
+    ms_p = _timed(b.run)
+    res_p = b.info_pool.clone()
+    ms_plain = _timed(b.run_plain)
+    same = bool(torch.equal(res_p, b.info_pool))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.run()
+    ms_g = _timed(graph.replay)
+    same_g = bool(torch.equal(res_p, b.info_pool))
+    bits = sum(int(r.shape[0]) * p["code"].K_info for r, p in zip(refs, parts))
+    errs = 0
+    for i, r in enumerate(refs):
+        info, _ = b.outputs(i)
+        errs += int((info != r).any(dim=1).sum())
+    b.close()
+    return dict(frames=total, contexts=len(names), launches=n_launch, tasks=n_tasks,
+                persistent=dict(value=bits / ms_p / 1e3, unit="Mb/s", ms=ms_p, frames_per_s=total / ms_p * 1e3),
+                plain_per_item=dict(value=bits / ms_plain / 1e3, unit="Mb/s", ms=ms_plain,
+                                    launches=len(parts)),
+                graph_replay=dict(value=bits / ms_g / 1e3, unit="Mb/s", ms=ms_g),
+                speedup_vs_plain=ms_plain / ms_p, identical_outputs=same and same_g, fer=errs / total)
+
+
+def run_c5(rates=(10e3, 50e3, 200e3, 1e6, 2e6), seconds=2.0, seed=11):
+    """Serving: Poisson arrivals of requests (1..256 frames) over five MCS
+    contexts; latency from arrival to observed completion, p50/p99."""
+    import time as _t
+    import torch
+    import synth
+    from paper_1710_08314_gb300.polarscl import Server
+    names = ["mcs_128_40", "mcs_256_128", "mcs_512_256", "mcs_1024_512", "mcs_2048_1723"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    ctxs, pools = [], []
+    R = 1024
+    for name in names:
+        d, code = _code(name)
+        _, llr = _gen_frames(code, 256 * 8, d["ebn0_db"], gen)
+        ctxs.append((code, d["L"], None))
+        pools.append((code, llr))
+    outs = [(torch.empty((R, 256, c.nbytes), dtype=torch.uint8, device="cuda"),
+             torch.empty((R, 256), dtype=torch.int32, device="cuda")) for c, _ in pools]
+    torch.cuda.synchronize()
+    res = {}
+    rng = np.random.default_rng(seed)
+    srv = Server(ctxs, ring_slots=R, max_frames=256, idle_timeout_ms=5000)
+    try:
+        for rate in rates:
+            mean_req = 128.5
+            req_rate = rate / mean_req
+            n_req = max(20, int(req_rate * seconds))
+            gaps = rng.exponential(1.0 / req_rate, n_req)
+            ctx = rng.integers(0, len(names), n_req)
+            sizes = rng.integers(1, 257, n_req)
+            arrive = {}
+            lat = []
+            frames_done = 0
+            t0 = _t.monotonic_ns()
+            sched = t0 + np.cumsum(gaps * 1e9).astype(np.int64)
+            i = 0
+            pending = 0
+            deadline = t0 + int((seconds + 30) * 1e9)
+            while (i < n_req or pending) and _t.monotonic_ns() < deadline:
+                now = _t.monotonic_ns()
+                while i < n_req and sched[i] <= now:
+                    k, n = int(ctx[i]), int(sizes[i])
+                    code, llr = pools[k]
+                    off = (i * 256) % (llr.shape[0] - 256)
+                    slot = i % R
+                    tk = srv.submit(k, llr[off:off + n], outs[k][0][slot, :n], outs[k][1][slot, :n])
+                    if tk is None:
+                        break  # full: deferred (arrival time kept)
+                    arrive[tk] = (int(sched[i]), n)
+                    i += 1
+                    pending += 1
+                for c in srv.poll():
+                    a, n = arrive.pop(c.ticket)
+                    lat.append((c.t_done_ns - a) / 1e6)
+                    frames_done += n
+                    pending -= 1
+            wall = (_t.monotonic_ns() - t0) / 1e9
+            log(f"serving rate {rate:.0f}: {len(lat)}/{n_req} requests, {pending} pending, {wall:.1f} s, "
+                f"status {srv.status()}")
+            lat.sort()
+            res[f"{int(rate)}"] = dict(offered_frames_per_s=rate, achieved_frames_per_s=frames_done / wall,
+                                       requests=len(lat), p50_ms=lat[len(lat) // 2] if lat else None,
+                                       p99_ms=lat[int(len(lat) * 0.99)] if lat else None,
+                                       max_ms=lat[-1] if lat else None)
+    finally:
+        srv.stop()
+    return res
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -180,6 +403,7 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--quant", default="f32", choices=list(QUANT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true", help="skip the further workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -189,7 +413,7 @@ def main():
     ws, rank, local = dist_env()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(n_frames_target=64, seed=99, max_seconds=20.0)  # before any CUDA use
+        cpu = cpu_oracle_rate(n_frames_target=100000, seed=99, max_seconds=20.0)  # before any CUDA use
 
     import numpy as np
     import torch
@@ -327,6 +551,29 @@ def main():
     if cpu:
         line["cpu_baseline"] = {"value": cpu[0], "unit": "Mb/s", "cores": cpu[1], "kind": "oracle",
                                 "sample": cpu[2]}
+    if not args.headline_only:
+        del llr, llr_h, llr_d
+        torch.cuda.empty_cache()
+        g2 = torch.Generator(device="cuda")
+        g2.manual_seed(77)
+        wl = {}
+        for key, fn in [("c1_cascl_128_64_L4", run_c1), ("c3_1024_512_L8", run_c3), ("c2_fa_2048_1723", run_c2),
+                        ("c4_uneven_500k", run_c4)]:
+            log(f"workload {key}")
+            try:
+                wl[key] = fn(g2)
+            except Exception as e:  # report, do not hide the headline
+                wl[key] = {"error": repr(e)}
+            torch.cuda.synchronize()
+        log("workload c5_serving")
+        try:
+            wl["c5_serving"] = run_c5()
+        except Exception as e:
+            wl["c5_serving"] = {"error": repr(e)}
+        line["workloads"] = wl
+        srv = wl.get("c5_serving", {})
+        p99 = [v.get("p99_ms") for v in srv.values() if isinstance(v, dict) and v.get("p99_ms") is not None]
+        line["p99_latency_ms_mixed_load"] = max(p99) if p99 else None
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -62,17 +62,20 @@ __device__ void srv_open(const SrvParams &S)
     atomicExch(&S.dev->opened, t);
 }
 
-// claim fpw frames of ticket k; returns the first frame, -1 if the slot holds
-// another ticket, -2 if every frame of k is taken
-__device__ int srv_claim(const SrvParams &S, uint32_t k, int n, int fpw)
+// try to claim fpw frames of ticket k whose claim word was just read as w
+// (tag k, next frame below n): a few compare-and-swaps, each retry using the
+// value the failed swap returned; -1 when others took everything first or
+// kept winning (the caller moves on to other requests)
+__device__ int srv_try_claim(const SrvParams &S, uint32_t k, unsigned long long w, int n, int fpw)
 {
     const int slot = (int)(k & (uint32_t)(S.R - 1));
-    for (int tries = 0; tries < 64; ++tries) {
-        const unsigned long long w = atomicAdd(&S.claim[slot], 0ull);
+    for (int tries = 0; tries < 4; ++tries) {
         if ((uint32_t)(w >> 32) != k) return -1;
         const int pos = (int)(uint32_t)w;
-        if (pos >= n) return -2;
-        if (atomicCAS(&S.claim[slot], w, w + (unsigned long long)fpw) == w) return pos;
+        if (pos >= n) return -1;
+        const unsigned long long old = atomicCAS(&S.claim[slot], w, w + (unsigned long long)fpw);
+        if (old == w) return pos;
+        w = old;
     }
     return -1;
 }
@@ -95,52 +98,78 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
     unsigned sleep_ns = 128;
     const bool poller = (gwarp & 7) == 0;   // a few warps watch the host words
     for (;;) {
-        // --- find a task (lane 0), broadcast it
+        // --- find a task: the 32 lanes look at 32 open requests at a time
         int k_found = -1, pos_found = -1, stop = 0, idle_out = 0;
+        uint32_t opened = 0, head = 0;
         if (c.lane == 0) {
             if (poller) {
                 if (*(volatile uint32_t *)&S.ctl->abort) atomicExch(&S.dev->abort, 1u);
                 srv_open(S);
             }
             stop = *(volatile uint32_t *)&S.dev->abort ? 1 : 0;
-            if (!stop) {
-                const uint32_t opened = *(volatile uint32_t *)&S.dev->opened;
-                __threadfence();
-                if (opened != seen_opened) {
-                    // new requests anywhere keep every warp alive
-                    seen_opened = opened;
-                    last_work = gtimer();
-                }
-                uint32_t head = *(volatile uint32_t *)&S.dev->head;
-                for (uint32_t k = head; k != opened && (int)(k - head) < S.R; ++k) {
-                    const int slot = (int)(k & (uint32_t)(S.R - 1));
-                    const SrvDReq &d = S.dreq[slot];
-                    const int ctx = ((volatile SrvDReq *)&d)->ctx;
-                    const int n = ((volatile SrvDReq *)&d)->n;
-                    if (ctx < 0 || ctx >= S.n_ctx) continue;
-                    const int fpw = 32 / S.K.items[ctx].L;
-                    const int pos = srv_claim(S, k, n, fpw);
-                    if (pos >= 0) {
-                        k_found = (int)k;
-                        pos_found = pos;
-                        break;
-                    }
-                    if (pos < 0 && k == head) {  // all frames taken, or the slot moved on
-                        atomicMax(&S.dev->head, k + 1);
-                        head = k + 1;
-                    }
+            opened = *(volatile uint32_t *)&S.dev->opened;
+            head = *(volatile uint32_t *)&S.dev->head;
+            if (opened != seen_opened) {
+                // new requests anywhere keep every warp alive
+                seen_opened = opened;
+                last_work = gtimer();
+            }
+        }
+        stop = __shfl_sync(PSCL_FULL, stop, 0);
+        if (stop) break;
+        opened = __shfl_sync(PSCL_FULL, opened, 0);
+        head = __shfl_sync(PSCL_FULL, head, 0);
+        __threadfence();
+        for (uint32_t base = head; base != opened && (int)(base - head) < S.R; base += 32) {
+            if (c.lane == 0) stop = *(volatile uint32_t *)&S.dev->abort ? 1 : 0;
+            stop = __shfl_sync(PSCL_FULL, stop, 0);
+            if (stop) break;
+            const uint32_t k = base + (uint32_t)c.lane;
+            const bool valid = (int)(k - base) < (int)(opened - base) && (int)(k - head) < S.R;
+            bool claimable = false, finished = false;  // lanes past `opened` never count
+            unsigned long long w = 0;
+            int n = 0, fpw = 1;
+            if (valid) {
+                const int slot = (int)(k & (uint32_t)(S.R - 1));
+                w = *(volatile unsigned long long *)&S.claim[slot];
+                const volatile SrvDReq *d = S.dreq + slot;
+                const int ctx = d->ctx;
+                n = d->n;
+                if ((uint32_t)(w >> 32) != k || (int)(uint32_t)w >= n) {
+                    finished = true;  // every frame taken (or the slot moved on)
+                } else if (ctx >= 0 && ctx < S.n_ctx) {
+                    claimable = true;
+                    fpw = 32 / S.K.items[ctx].L;
                 }
             }
-            if (!stop && k_found < 0 && gtimer() - last_work > S.idle_ns) {
-                atomicCAS(&S.ctl->exit_status, 0, PSCL_ETIMEDOUT);
-                idle_out = 1;
+            // requests from the head whose frames are all taken: move the head
+            const uint32_t fin = __ballot_sync(PSCL_FULL, finished);
+            const int run = fin == 0xFFFFFFFFu ? 32 : __ffs(~fin) - 1;
+            if (c.lane == 0 && base == head && run > 0) {
+                atomicMax(&S.dev->head, base + (uint32_t)run);
             }
+            uint32_t cand = __ballot_sync(PSCL_FULL, claimable);
+            while (cand) {
+                const int l = __ffs(cand) - 1;
+                int pos = -1;
+                if (c.lane == l) pos = srv_try_claim(S, k, w, n, fpw);
+                pos = __shfl_sync(PSCL_FULL, pos, l);
+                if (pos >= 0) {
+                    k_found = (int)__shfl_sync(PSCL_FULL, k, l);
+                    pos_found = pos;
+                    break;
+                }
+                cand &= cand - 1u;
+            }
+            if (k_found >= 0) break;
+        }
+        if (c.lane == 0 && !stop && k_found < 0 && gtimer() - last_work > S.idle_ns) {
+            atomicCAS(&S.ctl->exit_status, 0, PSCL_ETIMEDOUT);
+            idle_out = 1;
         }
         stop = __shfl_sync(PSCL_FULL, stop, 0);
         idle_out = __shfl_sync(PSCL_FULL, idle_out, 0);
         if (stop || idle_out) break;
-        k_found = __shfl_sync(PSCL_FULL, k_found, 0);
-        pos_found = __shfl_sync(PSCL_FULL, pos_found, 0);
         if (k_found < 0) {
             // idle: bounded wait (the budget is checked above)
             __nanosleep(sleep_ns);

@@ -126,3 +126,30 @@ def test_malformed_full_and_idle_are_reported_on_the_host():
         assert not stt["running"] and stt["device_status"] == ps.PSCL_ETIMEDOUT
     finally:
         srv.stop()
+
+
+def test_burst_of_large_requests_all_complete():
+    """Every idle warp races for the frames of the oldest request; no request
+    may be skipped while frames of it are still unclaimed."""
+    import torch
+    from paper_1710_08314_gb300.polarscl import Server
+    codes, ctx = _contexts()
+    reqs = []
+    for r in range(24):
+        k = 4 if r % 3 else 0          # mostly (2048, 1723) L = 32: one frame per task
+        d, g = codes[k]
+        n = 200 if k == 4 else 37
+        _, _, llr = make_inputs(d, n, d["ebn0_db"], 2000 + r)
+        reqs.append((k, torch.from_numpy(llr).cuda(), torch.zeros((n, g.nbytes), dtype=torch.uint8, device="cuda"),
+                     torch.zeros((n,), dtype=torch.int32, device="cuda")))
+    torch.cuda.synchronize()
+    srv = Server(ctx, ring_slots=32, max_frames=256, idle_timeout_ms=20000)
+    try:
+        tickets = [srv.submit(k, t, i, s) for k, t, i, s in reqs]
+        assert all(t is not None for t in tickets)
+        _wait(srv, tickets, timeout_s=120.0)
+    finally:
+        srv.stop()
+    for r, (k, t, i, s) in enumerate(reqs):
+        ri, rs = _reference(codes[k][1], t, codes[k][0]["L"])
+        assert torch.equal(ri, i) and torch.equal(rs, s), f"request {r} differs from pscl_decode"
