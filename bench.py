@@ -33,6 +33,17 @@ ALGO_CASCL = 1
 QUANT = {"f32": 0, "i16": 1, "i8": 2}
 
 
+def max_over_ranks(value: float, device: str = "cuda") -> float:
+    """Largest value over all ranks (the slowest rank's time), or the value
+    itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def log(msg):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
@@ -468,10 +479,7 @@ def main():
         dist.barrier()
     per_launch_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    t = torch.tensor([total_ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
     frames_all = B * args.steps * ws
     value = frames_all * K_info / (total_ms / 1e3) / 1e6
@@ -503,10 +511,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    te = torch.tensor([e0.elapsed_time(e1)], device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = frames_all * K_info / (float(te.item()) / 1e3) / 1e6
+    e2e_value = frames_all * K_info / (max_over_ranks(e0.elapsed_time(e1)) / 1e3) / 1e6
 
     if rank != 0:
         if dist:
