@@ -224,8 +224,10 @@ def run_c1(gen):
     """Plain CA-SCL (128, 64 incl. CRC-8), L = 4, f32, no pruning, 2.0 dB, 10,000 frames."""
     import torch
     from paper_1710_08314_gb300 import polarscl as ps
+    from paper_1710_08314_gb300 import autotune
     d, code = _code("c1_cascl_128_64_L4")
     info, llr = _gen_frames(code, 10000, 2.0, gen)
+    autotune.tuned(code, 4, 0, llr)
     out = torch.empty_like(info)
     st = torch.empty((10000,), dtype=torch.int32, device="cuda")
     ms = _timed(lambda: ps.pscl_decode(code.handle, llr, 10000, 4, 1, None, 0, out, st, None, None))
@@ -241,9 +243,12 @@ def run_c2(gen, snrs=(3.5, 4.0, 4.5), frames=200000):
     from paper_1710_08314_gb300 import pruning, polarscl as ps
     d, code = _code("c2_2048_1723")
     out = {}
+    from paper_1710_08314_gb300 import autotune
     for quant, qn, pr in [(0, "f32", pruning(15, rep_max=0)), (2, "i8", pruning(15, rep_max=8))]:
         for snr in snrs:
             info, llr = _gen_frames(code, frames, snr, gen)
+            if snr == snrs[-1]:
+                autotune.tuned(code, 32, quant, llr[:16384].contiguous(), prune=pr, algo=ps.PSCL_FASCL)
             o = torch.empty_like(info)
             st = torch.empty((frames,), dtype=torch.int32, device="cuda")
             ms = _timed(lambda: ps.pscl_decode(code.handle, llr, frames, 32, ps.PSCL_FASCL, pr, quant, o, st,
@@ -261,12 +266,14 @@ def run_c3(gen, snr=2.0, frames=100000):
     """CA-SCL (1024, 512 incl. CRC-16), L = 8: pruned vs unpruned, int16 and f32."""
     import torch
     from paper_1710_08314_gb300 import pruning, polarscl as ps
+    from paper_1710_08314_gb300 import autotune
     d, code = _code("c3_1024_512_L8")
     info, llr = _gen_frames(code, frames, snr, gen)
     o = torch.empty_like(info)
     st = torch.empty((frames,), dtype=torch.int32, device="cuda")
     out = {}
     for qn, quant in [("f32", 0), ("i16", 1)]:
+        autotune.tuned(code, 8, quant, llr[:8192].contiguous())
         for pn, pr in [("unpruned", None), ("pruned", pruning(15, rep_max=0))]:
             ms = _timed(lambda: ps.pscl_decode(code.handle, llr, frames, 8, 1, pr, quant, o, st, None, None))
             out[f"{qn}_{pn}"] = dict(value=frames * code.K_info / ms / 1e3, unit="Mb/s", frames=frames,
@@ -455,6 +462,9 @@ def main():
     info_out = torch.empty((B, code.nbytes), dtype=torch.uint8, device="cuda")
     status = torch.empty((B,), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    # schedule knobs from the autotuner (cached per GPU model and code)
+    from paper_1710_08314_gb300 import autotune
+    tuning, measured = autotune.tuned(code, L_LIST, quant, llr[:8192].contiguous())
 
     def step():
         ps.pscl_decode(code.handle, llr, B, L_LIST, ALGO_CASCL, None, quant, info_out, status, None, stream)
@@ -548,6 +558,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "Mb/s", "h2d_bytes_per_step": int(llr.numel() * 4),
                 "d2h_bytes_per_step": int(info_out.numel() + status.numel() * 4)},
         "gpu_launches": launches_per_step * args.steps,
+        "tuning": {"warps_per_sm": tuning[0], "fuse_leaves": tuning[1], "measured_now": measured},
         "roofline": roof,
         "clocks": clocks,
         "fer": fer, "crc_fail_rate": crc_fail,

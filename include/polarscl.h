@@ -111,7 +111,7 @@ int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
  * number format quant: warps_per_sm (1..32) sizes each warp's shared-memory
  * slice (more warps hide more latency, fewer keep more LLR layers on chip);
  * fuse_leaves (1, 2, 4, 8) is the largest unpruned subtree decoded in
- * registers.  (0, 0) restores the defaults (16 warps, 8 leaves).  Results
+ * registers.  (0, 0) restores the defaults (20 warps, 8 leaves).  Results
  * never depend on the tuning.  Written by the package's autotuner.         */
 int pscl_code_tune(pscl_code code, int L, pscl_quant quant, int warps_per_sm, int fuse_leaves);
 

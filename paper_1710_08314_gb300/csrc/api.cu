@@ -234,7 +234,7 @@ static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
 // shared-memory slice is sized for; per code and (L, format) the autotuner's
 // measurements override them (pscl_code_tune)
 static int g_fuse_max = 8;
-static int g_target_warps_per_sm = 16;
+static int g_target_warps_per_sm = 20;
 
 static void tuning_for(pscl_code c, int L, int quant, int *wps, int *fuse)
 {

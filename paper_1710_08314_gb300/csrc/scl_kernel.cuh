@@ -257,7 +257,7 @@ __device__ __forceinline__ void op_f(Ctx &c, int d)
     if (act) {
         if (H >= 4 * Qt::EPW) {
             const int HQ = H / (4 * Qt::EPW);
-#pragma unroll 2
+#pragma unroll 4
             for (int q = 0; q < HQ; ++q) {
                 const uint4 a = ld4(c, in, q, cin, win, cap_in, 1u);
                 const uint4 b = ld4(c, in, q + HQ, cin, win, cap_in, 1u);
@@ -302,7 +302,7 @@ __device__ __forceinline__ void op_g(Ctx &c, int d)
             for (int q0 = 0; q0 < HQ; q0 += QPB) {
                 const uint32_t bw = ld(c, bl, (q0 / QPB) * 32 + cs, cap_b, 4u);
                 const int cnt = HQ - q0 < QPB ? HQ - q0 : QPB;
-#pragma unroll 2
+#pragma unroll 4
                 for (int k = 0; k < cnt; ++k) {
                     const int q = q0 + k;
                     const uint4 a = ld4(c, in, q, cin, win, cap_in, 1u);
@@ -1131,8 +1131,9 @@ __device__ __forceinline__ void load_item(Ctx &c, const Item *src, const KParams
 // (uneven batches) the next task comes from a device counter, so warps that
 // drew short frames take more of them; otherwise warps stride over the
 // frames of the single item.
+// the node-free variant fits five blocks of four warps per SM (<= 102 registers)
 template <class Qt, bool NODES>
-__global__ void __launch_bounds__(128, 4) scl_kernel(const __grid_constant__ KParams K)
+__global__ void __launch_bounds__(128, NODES ? 4 : 5) scl_kernel(const __grid_constant__ KParams K)
 {
     extern __shared__ __align__(16) char smem[];
     Ctx c;
