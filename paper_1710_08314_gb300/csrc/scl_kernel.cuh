@@ -446,8 +446,9 @@ __device__ __forceinline__ void bitonic_seg(uint64_t (&k)[M], int L, int slot)
 // parent slot, candidate index and metric key.
 template <int M>
 __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], int &par, int &cand,
-                                             uint32_t &newkey, int &n_keep)
+                                             uint32_t &newkey, int &n_keep, bool &ident)
 {
+    ident = false;
     const int na = c.n_active;
     const int n_cand = na * M;
     if (n_cand <= c.L) {
@@ -464,6 +465,24 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
         return;
     }
     n_keep = c.L;
+    if (na == c.L) {
+        // every path's first candidate ranks before every other candidate:
+        // the first candidates survive in place, nothing is sorted
+        uint32_t mx = kp[0], mn = 0xFFFFFFFFu;
+#pragma unroll
+        for (int m = 1; m < M; ++m) mn = min(mn, kp[m]);
+        for (int o = 1; o < c.L; o <<= 1) {
+            mx = max(mx, __shfl_xor_sync(PSCL_FULL, mx, o));
+            mn = min(mn, __shfl_xor_sync(PSCL_FULL, mn, o));
+        }
+        if (__all_sync(PSCL_FULL, mn > mx)) {
+            par = c.slot;
+            cand = 0;
+            newkey = kp[0];
+            ident = true;
+            return;
+        }
+    }
     uint64_t k[M];
 #pragma unroll
     for (int m = 0; m < M; ++m)
@@ -634,17 +653,20 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
     uint32_t newkey;
     bool ident;
     if constexpr (M == 2) select_m2<Qt::VBITS>(c, kp[0], kp[1], par, cand, newkey, n_keep, ident);
-    else select_paths<M>(c, kp, par, cand, newkey, n_keep);
+    else select_paths<M>(c, kp, par, cand, newkey, n_keep, ident);
     const int pl = c.seg + par;
-    // the new path inherits its parent's slot tables (lazy copy)
-    c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
-    c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
-    c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
-    c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
-    const uint32_t hp = __shfl_sync(PSCL_FULL, h, pl);
-    uint32_t r0 = __shfl_sync(PSCL_FULL, rp[0], pl);
-    uint32_t r1 = __shfl_sync(PSCL_FULL, rp[1], pl);
-    uint32_t r2 = __shfl_sync(PSCL_FULL, rp[2], pl);
+    uint32_t hp = h, r0 = rp[0], r1 = rp[1], r2 = rp[2];
+    if (!ident) {
+        // the new path inherits its parent's slot tables (lazy copy)
+        c.idxL[0] = __shfl_sync(PSCL_FULL, c.idxL[0], pl);
+        c.idxL[1] = __shfl_sync(PSCL_FULL, c.idxL[1], pl);
+        c.idxS[0] = __shfl_sync(PSCL_FULL, c.idxS[0], pl);
+        c.idxS[1] = __shfl_sync(PSCL_FULL, c.idxS[1], pl);
+        hp = __shfl_sync(PSCL_FULL, h, pl);
+        r0 = __shfl_sync(PSCL_FULL, rp[0], pl);
+        r1 = __shfl_sync(PSCL_FULL, rp[1], pl);
+        r2 = __shfl_sync(PSCL_FULL, rp[2], pl);
+    }
     pm = Qt::from_key(newkey);
     if (type == NT_REP) {
         const uint32_t ones = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
@@ -664,6 +686,15 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
             for (int k = 0; k < 5; ++k)
                 if (k < t && ((j >> k) & 1)) b ^= 1u << (pos[k] & 31u);
             st(c, dst, c.lane, capd, b, 64u);
+        } else if (ident) {
+            // own hard decisions are already in place: apply the flips only
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k < t && ((j >> k) & 1)) {
+                    const int w = (int)(pos[k] >> 5);
+                    st(c, dst, w * 32 + c.lane, capd, ld(c, dst, w * 32 + c.lane, capd, 128u) ^ (1u << (pos[k] & 31u)),
+                       64u);
+                }
         } else {
             const int W = S >> 5;
             for (int w = 0; w < W; ++w) {
