@@ -405,6 +405,25 @@ def run_c5(rates=(10e3, 50e3, 200e3, 1e6, 2e6), seconds=2.0, seed=11):
     return res
 
 
+def profiled_traffic(frames: int):
+    """DRAM bytes of one decode launch of `frames` frames, scaled from the ncu
+    capture summarised in profiles/ (traffic grows with the frame count), or
+    None when the kernel sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "scl_kernel_f32_cascl_2048_1723_L32_unpruned.md")
+    csrc = os.path.join(ROOT, "paper_1710_08314_gb300", "csrc")
+    try:
+        txt = open(path).read()
+        per = int(txt.split("dram_bytes_per_frame:")[1].split()[0])
+        sha = txt.split("kernel_sources_sha1:")[1].split()[0]
+        h = hashlib.sha1()
+        for f in ("scl_kernel.cuh", "internal.h", "api.cu"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        return per * frames if h.hexdigest()[:16] == sha else None
+    except (OSError, IndexError, ValueError):
+        return None
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -543,7 +562,8 @@ def main():
         peak_gops = sms * 128 * mhz * 1e6 / 1e9
         achieved = work["fg_elems"] * B / avg_launch_s / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                "frac": achieved / peak_gops, "traffic": None,
+                "frac": achieved / peak_gops,
+                "traffic": profiled_traffic(B) if args.quant == "f32" else None,
                 "note": (f"f/g LLR updates ({work['fg_elems']} per frame) per second vs one update per "
                          f"FP32 lane per clock ({sms} SMs x 128 lanes x {mhz:.0f} MHz sampled)")}
     line = {
