@@ -257,8 +257,26 @@ __device__ __forceinline__ void op_f(Ctx &c, int d)
     if (act) {
         if (H >= 4 * Qt::EPW) {
             const int HQ = H / (4 * Qt::EPW);
-#pragma unroll 4
-            for (int q = 0; q < HQ; ++q) {
+            // blocks of four quad pairs: all eight loads are issued before
+            // any store (the buffers could alias as far as the compiler
+            // knows, so it would not hoist them itself)
+            constexpr int U = 4;
+            int q = 0;
+            for (; q + U <= HQ; q += U) {
+                uint4 a[U], b[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    a[u] = ld4(c, in, q + u, cin, win, cap_in, 1u);
+                    b[u] = ld4(c, in, q + u + HQ, cin, win, cap_in, 1u);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    st4(c, out, q + u, c.lane, cap_out,
+                        make_uint4(Qt::F(a[u].x, b[u].x), Qt::F(a[u].y, b[u].y), Qt::F(a[u].z, b[u].z),
+                                   Qt::F(a[u].w, b[u].w)),
+                        2u);
+            }
+            for (; q < HQ; ++q) {
                 const uint4 a = ld4(c, in, q, cin, win, cap_in, 1u);
                 const uint4 b = ld4(c, in, q + HQ, cin, win, cap_in, 1u);
                 st4(c, out, q, c.lane, cap_out,
@@ -299,21 +317,33 @@ __device__ __forceinline__ void op_g(Ctx &c, int d)
         if (H >= 4 * Qt::EPW) {
             const int HQ = H / (4 * Qt::EPW);
             constexpr int QPB = 32 / (4 * Qt::EPW);  // quads per 32-bit beta word
-            for (int q0 = 0; q0 < HQ; q0 += QPB) {
-                const uint32_t bw = ld(c, bl, (q0 / QPB) * 32 + cs, cap_b, 4u);
-                const int cnt = HQ - q0 < QPB ? HQ - q0 : QPB;
-#pragma unroll 4
-                for (int k = 0; k < cnt; ++k) {
-                    const int q = q0 + k;
-                    const uint4 a = ld4(c, in, q, cin, win, cap_in, 1u);
-                    const uint4 b = ld4(c, in, q + HQ, cin, win, cap_in, 1u);
-                    const uint32_t sb = bw >> (k * 4 * Qt::EPW);
-                    st4(c, out, q, c.lane, cap_out,
-                        make_uint4(Qt::G(a.x, b.x, sb & M1), Qt::G(a.y, b.y, (sb >> Qt::EPW) & M1),
-                                   Qt::G(a.z, b.z, (sb >> (2 * Qt::EPW)) & M1),
-                                   Qt::G(a.w, b.w, (sb >> (3 * Qt::EPW)) & M1)),
-                        2u);
+            auto sbits = [&](int q) {
+                const uint32_t bw = ld(c, bl, (q / QPB) * 32 + cs, cap_b, 4u);
+                return bw >> ((q % QPB) * 4 * Qt::EPW);
+            };
+            auto gq = [&](const uint4 &a, const uint4 &b, uint32_t sb) {
+                return make_uint4(Qt::G(a.x, b.x, sb & M1), Qt::G(a.y, b.y, (sb >> Qt::EPW) & M1),
+                                  Qt::G(a.z, b.z, (sb >> (2 * Qt::EPW)) & M1),
+                                  Qt::G(a.w, b.w, (sb >> (3 * Qt::EPW)) & M1));
+            };
+            constexpr int U = 4;
+            int q = 0;
+            for (; q + U <= HQ; q += U) {
+                uint4 a[U], b[U];
+                uint32_t sb[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    a[u] = ld4(c, in, q + u, cin, win, cap_in, 1u);
+                    b[u] = ld4(c, in, q + u + HQ, cin, win, cap_in, 1u);
+                    sb[u] = sbits(q + u);
                 }
+#pragma unroll
+                for (int u = 0; u < U; ++u) st4(c, out, q + u, c.lane, cap_out, gq(a[u], b[u], sb[u]), 2u);
+            }
+            for (; q < HQ; ++q) {
+                const uint4 a = ld4(c, in, q, cin, win, cap_in, 1u);
+                const uint4 b = ld4(c, in, q + HQ, cin, win, cap_in, 1u);
+                st4(c, out, q, c.lane, cap_out, gq(a, b, sbits(q)), 2u);
             }
         } else if (H >= Qt::EPW) {
             const int HW = H / Qt::EPW;
@@ -345,7 +375,21 @@ __device__ __forceinline__ void op_comb(Ctx &c, int d, int parent_side)
     const int cl = c.seg + tab_get(c.idxS, d);
     if (S >= 32) {
         const int W = S >> 5;
-        for (int w = 0; w < W; ++w) {
+        int w = 0;
+        for (; w + 4 <= W; w += 4) {  // loads first: the buffers could alias for the compiler
+            uint32_t l[4], r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                l[u] = ld(c, bl, (w + u) * 32 + cl, cap, 8u);
+                r[u] = ld(c, br, (w + u) * 32 + c.lane, cap, 8u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                st(c, dst, (w + u) * 32 + c.lane, capd, l[u] ^ r[u], 16u);
+                st(c, dst, (w + u + W) * 32 + c.lane, capd, r[u], 16u);
+            }
+        }
+        for (; w < W; ++w) {
             uint32_t l = ld(c, bl, w * 32 + cl, cap, 8u);
             uint32_t r = ld(c, br, w * 32 + c.lane, cap, 8u);
             st(c, dst, w * 32 + c.lane, capd, l ^ r, 16u);
