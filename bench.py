@@ -297,8 +297,8 @@ def run_c3(gen, snr=2.0, frames=100000):
     st = torch.empty((frames,), dtype=torch.int32, device="cuda")
     out = {}
     for qn, quant in [("f32", 0), ("i16", 1)]:
-        autotune.tuned(code, 8, quant, llr[:8192].contiguous())
         for pn, pr in [("unpruned", None), ("pruned", pruning(15, rep_max=0))]:
+            autotune.tuned(code, 8, quant, llr[:16384].contiguous(), prune=pr)
             ms = _timed(lambda: ps.pscl_decode(code.handle, llr, frames, 8, 1, pr, quant, o, st, None, None))
             out[f"{qn}_{pn}"] = dict(value=frames * code.K_info / ms / 1e3, unit="Mb/s", frames=frames,
                                      fer=float((o != info).any(dim=1).float().mean()), ms=ms)

@@ -107,13 +107,15 @@ int pscl_code_info(pscl_code code, int *N, int *K, int *K_info, int *n_punctured
  * first build makes a synchronous upload.                                   */
 int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
 
-/* Record measured tuning for decodes of this code with list size L and
- * number format quant: warps_per_sm (1..32) sizes each warp's shared-memory
+/* Record measured tuning for decodes of this code with list size L, number
+ * format quant and pruning (NULL or mask 0 = the unpruned entry, anything
+ * else = the pruned entry): warps_per_sm (1..32) sizes each warp's shared-memory
  * slice (more warps hide more latency, fewer keep more LLR layers on chip);
  * fuse_leaves (1, 2, 4, 8) is the largest unpruned subtree decoded in
  * registers.  (0, 0) restores the defaults (20 warps, 8 leaves).  Results
  * never depend on the tuning.  Written by the package's autotuner.         */
-int pscl_code_tune(pscl_code code, int L, pscl_quant quant, int warps_per_sm, int fuse_leaves);
+int pscl_code_tune(pscl_code code, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
+                   int fuse_leaves);
 
 /* Decode n_frames frames (Algorithm 1 with the selected algorithm).
  * llr: device, n_frames x (N - P) float32, row-major.

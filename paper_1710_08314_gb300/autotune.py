@@ -72,7 +72,7 @@ def measure(code, llr, L, quant, prune=None, algo=ps.PSCL_CASCL, warps_grid=WARP
     results = []
     for w in warps_grid:
         for f in fuse_grid:
-            ps.pscl_code_tune(code.handle, L, quant, w, f)
+            ps.pscl_code_tune(code.handle, L, quant, w, f, prune)
             ps.pscl_decode(code.handle, llr, n, L, algo, prune, quant, info, status, None, None)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -96,12 +96,12 @@ def tuned(code, L, quant, llr_sample=None, prune=None, algo=ps.PSCL_CASCL, path:
         cache = load_cache(path)
     hit = cache.get(key)
     if hit and not remeasure:
-        ps.pscl_code_tune(code.handle, L, quant, hit["warps_per_sm"], hit["fuse"])
+        ps.pscl_code_tune(code.handle, L, quant, hit["warps_per_sm"], hit["fuse"], prune)
         return (hit["warps_per_sm"], hit["fuse"]), False
     if llr_sample is None:
         return None, False
     results, best = measure(code, llr_sample, L, quant, prune, algo)
-    ps.pscl_code_tune(code.handle, L, quant, best["warps_per_sm"], best["fuse"])
+    ps.pscl_code_tune(code.handle, L, quant, best["warps_per_sm"], best["fuse"], prune)
     with _lock:
         cache = load_cache(path)
         cache[key] = dict(warps_per_sm=best["warps_per_sm"], fuse=best["fuse"], ms=best["ms"],

@@ -236,12 +236,17 @@ static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
 static int g_fuse_max = 8;
 static int g_target_warps_per_sm = 20;
 
-static void tuning_for(pscl_code c, int L, int quant, int *wps, int *fuse)
+static int tune_key(int L, int quant, const pscl_pruning *pr)
+{
+    return L * 8 + quant + ((pr && pr->mask) ? 1024 : 0);
+}
+
+static void tuning_for(pscl_code c, int L, int quant, const pscl_pruning *pr, int *wps, int *fuse)
 {
     *wps = g_target_warps_per_sm;
     *fuse = g_fuse_max;
     std::lock_guard<std::mutex> lk(c->mu);
-    auto it = c->tune.find(L * 8 + quant);
+    auto it = c->tune.find(tune_key(L, quant, pr));
     if (it != c->tune.end()) {
         *wps = it->second.first;
         *fuse = it->second.second;
@@ -375,20 +380,21 @@ extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
     return PSCL_OK;
 }
 
-extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, int warps_per_sm, int fuse_leaves)
+extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
+                              int fuse_leaves)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
     if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return fail(PSCL_EINVAL, "L=%d", L);
     if (quant < PSCL_F32 || quant > PSCL_I8) return fail(PSCL_EINVAL, "unknown quantisation %d", (int)quant);
     std::lock_guard<std::mutex> lk(c->mu);
     if (warps_per_sm == 0 && fuse_leaves == 0) {
-        c->tune.erase(L * 8 + (int)quant);
+        c->tune.erase(tune_key(L, (int)quant, pruning));
         return PSCL_OK;
     }
     if (warps_per_sm < 1 || warps_per_sm > 32) return fail(PSCL_EINVAL, "warps per SM %d out of 1..32", warps_per_sm);
     if (fuse_leaves != 1 && fuse_leaves != 2 && fuse_leaves != 4 && fuse_leaves != 8)
         return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8", fuse_leaves);
-    c->tune[L * 8 + (int)quant] = std::make_pair(warps_per_sm, fuse_leaves);
+    c->tune[tune_key(L, (int)quant, pruning)] = std::make_pair(warps_per_sm, fuse_leaves);
     return PSCL_OK;
 }
 
@@ -490,7 +496,7 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     CU(cudaGetDevice(&dev));
     if (dev != c->dev) return fail(PSCL_EINVAL, "code was created on device %d, current device is %d", c->dev, dev);
     int wps, fuse;
-    tuning_for(c, L, (int)quant, &wps, &fuse);
+    tuning_for(c, L, (int)quant, pr, &wps, &fuse);
     int rc = build_program ? get_program(c, pr, fuse, &pl->pg) : find_program(c, pr, fuse, &pl->pg);
     if (rc) return rc;
     DevProps dp;
@@ -862,7 +868,7 @@ extern "C" int pscl_batch_create(const pscl_work_item *items, int n_items, pscl_
             return fail(PSCL_EINVAL, "item %d: bad quantisation or frame count", i);
         }
         int wps_i, fuse_i;
-        tuning_for(w.code, w.algo == PSCL_SC ? 1 : w.L, (int)w.quant, &wps_i, &fuse_i);
+        tuning_for(w.code, w.algo == PSCL_SC ? 1 : w.L, (int)w.quant, w.pruning, &wps_i, &fuse_i);
         rc = get_program(w.code, w.pruning, fuse_i, &progs[(size_t)i]);
         if (rc) { batch_free(b); return rc; }
     }
@@ -1129,7 +1135,7 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
             return fail(PSCL_EINVAL, "context %d: L=%d", i, cx.L);
         }
         int wps, fuse;
-        tuning_for(cx.code, cx.L, s->quant, &wps, &fuse);
+        tuning_for(cx.code, cx.L, s->quant, cx.pruning, &wps, &fuse);
         Program pg;
         rc = get_program(cx.code, cx.pruning, fuse, &pg);
         if (rc) { server_free(s); return rc; }

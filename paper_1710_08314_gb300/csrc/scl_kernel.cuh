@@ -240,6 +240,23 @@ __device__ __forceinline__ uint64_t shfl64_xor(uint64_t v, int m)
     return ((uint64_t)hi << 32) | lo;
 }
 
+// words w0..w0+3 of a column (w0 a multiple of 4), one 16-byte access when
+// all four exist
+__device__ __forceinline__ void fetch4(const Ctx &c, const uint32_t *p, int w0, int nw, int col, int width,
+                                       uint32_t cap, uint32_t (&out)[4])
+{
+    if (nw - w0 >= 4) {
+        const uint4 v = ld4(c, p, w0 >> 2, col, width, cap, 1u);
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+        out[3] = v.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = w0 + k < nw ? ld(c, p, qa(w0 + k, col, width), cap, 1u) : 0u;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // f step at depth d: layer d+1 (own column) = f(layer d) for the left child.
 // Slots without an active path skip the memory traffic (their columns are
@@ -433,9 +450,13 @@ __device__ __forceinline__ void normalise(Ctx &c, typename Qt::V &pm)
 {
     if (!Qt::FIXED) return;
     typename Qt::V v = c.slot < c.n_active ? pm : Qt::big();
-    for (int m = 1; m < c.L; m <<= 1) {
-        typename Qt::V o = __shfl_xor_sync(PSCL_FULL, v, m);
-        v = o < v ? o : v;
+    if (c.L == 32) {
+        v = (typename Qt::V)__reduce_min_sync(PSCL_FULL, (int)v);
+    } else {
+        for (int m = 1; m < c.L; m <<= 1) {
+            typename Qt::V o = __shfl_xor_sync(PSCL_FULL, v, m);
+            v = o < v ? o : v;
+        }
     }
     pm = Qt::sub(pm, v);
 }
@@ -512,14 +533,12 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
     if (na == c.L) {
         // every path's first candidate ranks before every other candidate:
         // the first candidates survive in place, nothing is sorted
-        uint32_t mx = kp[0], mn = 0xFFFFFFFFu;
+        uint32_t mn = 0xFFFFFFFFu;
 #pragma unroll
         for (int m = 1; m < M; ++m) mn = min(mn, kp[m]);
-        for (int o = 1; o < c.L; o <<= 1) {
-            mx = max(mx, __shfl_xor_sync(PSCL_FULL, mx, o));
-            mn = min(mn, __shfl_xor_sync(PSCL_FULL, mn, o));
-        }
-        if (__all_sync(PSCL_FULL, mn > mx)) {
+        const uint32_t mx = __reduce_max_sync(PSCL_FULL, kp[0]);
+        mn = __reduce_min_sync(PSCL_FULL, mn);
+        if (mn > mx) {
             par = c.slot;
             cand = 0;
             newkey = kp[0];
@@ -599,13 +618,13 @@ __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int 
     const bool act = c.slot < na;
     const uint32_t a = act ? ka : 0xFFFFFFFFu, b = act ? kb : 0xFFFFFFFFu;
     if (na == L) {
-        uint32_t mx = a, mn = b;
-        for (int m = 1; m < L; m <<= 1) {
-            mx = max(mx, __shfl_xor_sync(PSCL_FULL, mx, m));
-            mn = min(mn, __shfl_xor_sync(PSCL_FULL, mn, m));
-        }
-        // every frame of the warp must agree: the shuffles below are warp-wide
-        if (__all_sync(PSCL_FULL, mn > mx)) {
+        // warp-wide reductions (one instruction each): when every flip
+        // candidate of the warp ranks after every keep candidate, each frame
+        // of the warp keeps its paths in place (a sufficient condition per
+        // frame, and the same decision in every lane)
+        const uint32_t mx = __reduce_max_sync(PSCL_FULL, a);
+        const uint32_t mn = __reduce_min_sync(PSCL_FULL, b);
+        if (mn > mx) {
             par = c.slot;
             cand = 0;
             newkey = ka;
@@ -773,15 +792,19 @@ __device__ __forceinline__ void op_node(Ctx &c, int d, int type, int side, int t
         TreeSum<Qt> t0, t1;
         V p0 = Qt::zero(), p1 = Qt::zero();
         const int nw = (S + Qt::EPW - 1) / Qt::EPW;
-        for (int w = 0; w < nw; ++w) {
-            const uint32_t wd = ld(c, in, qa(w, cin, win), cap_in, 1u);
+        for (int w0 = 0; w0 < nw; w0 += 4) {
+            uint32_t wq[4];
+            fetch4(c, in, w0, nw, cin, win, cap_in, wq);
 #pragma unroll
-            for (int e = 0; e < Qt::EPW; ++e) {
-                const int i = w * Qt::EPW + e;
-                if (i < S) {
-                    const V v = Qt::elem(wd, e);
-                    p0 = t0.push(v < 0 ? Qt::absv(v) : Qt::zero(), i);
-                    if (type == NT_REP) p1 = t1.push(v > 0 ? Qt::absv(v) : Qt::zero(), i);
+            for (int k4 = 0; k4 < 4; ++k4) {
+#pragma unroll
+                for (int e = 0; e < Qt::EPW; ++e) {
+                    const int i = (w0 + k4) * Qt::EPW + e;
+                    if (i < S) {
+                        const V v = Qt::elem(wq[k4], e);
+                        p0 = t0.push(v < 0 ? Qt::absv(v) : Qt::zero(), i);
+                        if (type == NT_REP) p1 = t1.push(v > 0 ? Qt::absv(v) : Qt::zero(), i);
+                    }
                 }
             }
         }
@@ -810,13 +833,15 @@ __device__ __forceinline__ void op_node(Ctx &c, int d, int type, int side, int t
     uint32_t hword = 0, hlast = 0;
     int parity = 0;
     const int nw = (S + Qt::EPW - 1) / Qt::EPW;
-    for (int w = 0; w < nw; ++w) {
-        const uint32_t wd = ld(c, in, qa(w, cin, win), cap_in, 1u);
+    for (int w0 = 0; w0 < nw; w0 += 4) {
+        uint32_t wq[4];
+        fetch4(c, in, w0, nw, cin, win, cap_in, wq);
 #pragma unroll
-        for (int e = 0; e < Qt::EPW; ++e) {
-            const int i = w * Qt::EPW + e;
+        for (int ee = 0; ee < 4 * Qt::EPW; ++ee) {
+            const int e = ee % Qt::EPW;
+            const int i = w0 * Qt::EPW + ee;
             if (i < S) {
-                const V v = Qt::elem(wd, e);
+                const V v = Qt::elem(wq[ee / Qt::EPW], e);
                 const V a = Qt::absv(v);
                 hword |= (uint32_t)(v < 0) << (i & 31);
                 if (a < bv[4]) {
