@@ -156,13 +156,38 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
         for (int k = 0; k < 8; k++) r = (r & 0x80000000u) ? ((r << 1) ^ p32) : (r << 1);
         lut[b] = r;
     }
+    // CRC check as a syndrome (Sec. IV-A): with the register starting at 0
+    // the check "remainder of the first kinfo bits of u_A equals its last
+    // crc_len bits" is linear over GF(2), so every position of A has a
+    // crc_len-bit column and a path passes when the XOR of the columns of
+    // its one-bits is 0.  Tabulated per codeword byte and byte value.
+    const int NB = N >> 3;
+    std::vector<uint32_t> syn((size_t)NB * 256, 0);
+    if (crc_len > 0) {
+        std::vector<uint32_t> poscol(N, 0);
+        uint32_t r = p32;  // register after a lone one-bit at the last info index
+        for (int k = c->kinfo - 1; k >= 0; --k) {
+            poscol[A[k]] = r >> (32 - crc_len);
+            r = (r & 0x80000000u) ? ((r << 1) ^ p32) : (r << 1);
+        }
+        for (int k = c->kinfo; k < K; ++k) poscol[A[k]] = 1u << (K - 1 - k);
+        for (int q = 0; q < NB; ++q)
+            for (int v = 0; v < 256; ++v) {
+                uint32_t e = 0;
+                for (int b = 0; b < 8; ++b)
+                    if ((v >> b) & 1) e ^= poscol[8 * q + b];
+                syn[(size_t)q * 256 + v] = e;
+            }
+    }
     size_t off_in = 0, off_A = off_in + 4 * (size_t)N, off_am = off_A + ((2 * (size_t)K + 15) & ~(size_t)15),
-           off_lut = off_am + ((4 * (size_t)NW + 15) & ~(size_t)15), total = off_lut + 1024;
+           off_lut = off_am + ((4 * (size_t)NW + 15) & ~(size_t)15), off_syn = off_lut + 1024,
+           total = off_syn + 4 * syn.size();
     std::vector<uint8_t> blob(total, 0);
     memcpy(blob.data() + off_in, in_index.data(), 4 * (size_t)N);
     memcpy(blob.data() + off_A, A.data(), 2 * (size_t)K);
     memcpy(blob.data() + off_am, amask.data(), 4 * (size_t)NW);
     memcpy(blob.data() + off_lut, lut.data(), 1024);
+    memcpy(blob.data() + off_syn, syn.data(), 4 * syn.size());
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_blob, total);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), total, cudaMemcpyHostToDevice);
@@ -186,6 +211,7 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
     dc.A = (const uint16_t *)(base + off_A);
     dc.amask = (const uint32_t *)(base + off_am);
     dc.crc_lut = (const uint32_t *)(base + off_lut);
+    dc.syn = (const uint32_t *)(base + off_syn);
     *out = c;
     return PSCL_OK;
 }

@@ -43,6 +43,7 @@ struct DevCode {
     const uint16_t *A;          // K information positions, increasing
     const uint32_t *amask;      // max(1, N/32) words: bit set for positions in A
     const uint32_t *crc_lut;    // 256 entries, MSB-first table for the 32-bit-aligned CRC
+    const uint32_t *syn;        // N/8 x 256: CRC syndrome contribution of codeword byte q with value v
 };
 
 // Per-warp memory map.  Offsets are bytes inside the warp's shared-memory

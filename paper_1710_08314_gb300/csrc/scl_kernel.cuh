@@ -1038,35 +1038,30 @@ __device__ __forceinline__ uint32_t uword(const Ctx &c, int w, int col, int cl)
     return ld(c, ns, w * 32 + col, c.P->lay.ns_words, 512u);
 }
 
-// CRC check of the lane's path (Sec. IV-A): bits of u_A in order, the first
-// K_info feed the CRC register (MSB first, 32-bit aligned), the last c are
-// compared with the remainder.
+// CRC check of the lane's path (Sec. IV-A): the first K_info bits of u_A feed
+// the CRC register (MSB first, starting at 0), the last c are compared with
+// the remainder.  The comparison is linear in the codeword, so it is computed
+// as a syndrome: one table lookup per codeword byte (XOR of the columns of the
+// byte's one-bits), zero when the check passes.
 static __device__ bool crc_check(const Ctx &c, int cl)
 {
     const DevCode &cd = c.P->code;
     if (cd.crc_len == 0) return true;
-    const int NW = c.N >= 32 ? c.N >> 5 : 1;
-    uint32_t reg = 0, recv = 0;
-    int k = 0;
-    for (int w = 0; w < NW; ++w) {
-        uint32_t am = __ldg(&cd.amask[w]);
-        if (!am) continue;
-        const uint32_t x = uword(c, w, c.lane, cl);
-        while (am) {
-            const int b = __ffs(am) - 1;
-            am &= am - 1u;
-            const uint32_t bit = (x >> b) & 1u;
-            if (k < cd.kinfo) {
-                const uint32_t top = reg >> 31;
-                reg <<= 1;
-                if (top ^ bit) reg ^= cd.poly32;
-            } else {
-                recv = (recv << 1) | bit;
+    const int NB = c.N >> 3;
+    uint32_t s = 0;
+    for (int w0 = 0; w0 * 4 < NB; w0 += 4) {
+        uint32_t x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = (w0 + u) * 4 < NB ? uword(c, w0 + u, c.lane, cl) : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = (w0 + u) * 4 + j;
+                if (q < NB) s ^= __ldg(&cd.syn[(q << 8) | ((x[u] >> (8 * j)) & 0xFFu)]);
             }
-            ++k;
-        }
     }
-    return (reg >> (32 - cd.crc_len)) == recv;
+    return s == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1171,12 +1166,16 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         }
         const int nbytes = (cd.kinfo + 7) >> 3;
         for (int b = c.slot; b < nbytes; b += c.L) {
-            uint32_t byte = 0;
+            uint32_t byte = 0, wv = 0;
+            int cw = -1;  // positions increase: reload only when the word changes
             for (int k = 0; k < 8; ++k) {
                 const int i = 8 * b + k;
                 if (i < cd.kinfo) {
                     const int pz = __ldg(&cd.A[i]);
-                    const uint32_t wv = uword(c, pz >> 5, wcol, wcl);
+                    if ((pz >> 5) != cw) {
+                        cw = pz >> 5;
+                        wv = uword(c, cw, wcol, wcl);
+                    }
                     byte |= ((wv >> (pz & 31)) & 1u) << (7 - k);
                 }
             }
