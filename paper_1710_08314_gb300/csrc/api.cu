@@ -313,6 +313,14 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, i
         if (d > max_depth) max_depth = d;
         return PSCL_OK;
     }
+    if (d >= 1 && fuse >= 2 && S == 2 * fuse && subtree_unpruned(c, pr, o, S)) {
+        // f, both register subtrees, g and h in one step
+        uint32_t fz = 0;
+        for (int i = 0; i < S; i++) fz |= (uint32_t)c->frozen[o + i] << i;
+        ops.push_back(op_make(OP_RSUB2, (uint32_t)d, 0, (uint32_t)side, 0) | (fz << 16));
+        if (d > max_depth) max_depth = d;
+        return PSCL_OK;
+    }
     ops.push_back(op_make(OP_F, (uint32_t)d, 0, 0, 0));
     int rc = gen_program(c, pr, fuse, d + 1, o, S / 2, 0, ops, max_depth);
     if (rc) return rc;

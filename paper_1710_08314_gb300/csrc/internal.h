@@ -21,6 +21,10 @@ enum Opcode : uint32_t {
     OP_COMB = 3,  // right child at depth d done: parent beta = h(left, right)
     OP_RSUB = 4,  // unpruned subtree of 2..8 leaves at depth d, decoded in
                   //   registers; bits 16..31: frozen mask of its leaves
+    OP_RSUB2 = 5, // unpruned subtree of 2H leaves (H = 2..8) at depth d: f,
+                  //   left half in registers, g, right half in registers, h;
+                  //   the node's LLRs are read twice from layer d and its
+                  //   children's LLRs never reach memory; bits 16..31 as above
 };
 enum NodeType : uint32_t { NT_R0 = 1, NT_R1 = 2, NT_REP = 3, NT_SPC = 4 };
 

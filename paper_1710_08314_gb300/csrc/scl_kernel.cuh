@@ -984,6 +984,55 @@ __device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, ty
     if (side == 0) tab_set(c.idxS, d, c.slot);
 }
 
+// An unpruned node of 2H leaves at depth d: the f step, the left subtree in
+// registers, the g step (the node's LLRs read again from the column the path
+// holds after the left half's selections), the right subtree in registers and
+// the h step, with the left half's partial sums following the path through
+// the right half's selections.  Equivalent to F, RSUB, G, RSUB, COMB.
+template <class Qt, int H>
+__device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, uint32_t fz, typename Qt::V &pm)
+{
+    typedef typename Qt::V V;
+    constexpr int S = 2 * H;
+    constexpr int NW = (S + Qt::EPW - 1) / Qt::EPW;
+    const uint32_t *in = llr_layer(c, d);
+    const uint32_t cap = c.P->lay.llr_words[d];
+    uint32_t bl = 0u, br = 0u;
+    auto carry = [&](int pl) { bl = __shfl_sync(PSCL_FULL, bl, pl); };
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int cin = c.seg + tab_get(c.idxL, d);
+        uint32_t wd[NW];
+        if constexpr (NW >= 4) {
+#pragma unroll
+            for (int q = 0; q < NW / 4; ++q) {
+                const uint4 v = ld4(c, in, q, cin, 32, cap, 1u);
+                wd[4 * q] = v.x;
+                wd[4 * q + 1] = v.y;
+                wd[4 * q + 2] = v.z;
+                wd[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) wd[w] = ld(c, in, qa(w, cin, 32), cap, 1u);
+        }
+        V a[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const V x = Qt::elem(wd[i / Qt::EPW], i % Qt::EPW);
+            const V y = Qt::elem(wd[(i + H) / Qt::EPW], (i + H) % Qt::EPW);
+            a[i] = half == 0 ? Qt::f1(x, y) : Qt::g1(x, y, (bl >> i) & 1u);
+        }
+        const uint32_t beta = rsub<Qt, H>(c, a, fz >> (half * H), pm, carry);
+        if (half == 0) bl = beta;
+        else br = beta;
+    }
+    constexpr uint32_t m = (1u << H) - 1u;
+    uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
+    st(c, dst, c.lane, c.P->lay.b_words[d], ((bl ^ br) & m) | ((br & m) << H), 64u);
+    if (side == 0) tab_set(c.idxS, d, c.slot);
+}
+
 // ---------------------------------------------------------------------------
 // codeword word w (32 positions) of the lane's path (or of slot `col`'s path
 // with its BL_1 column `cl`) once the root is complete
@@ -1123,6 +1172,15 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
             case 4: op_rsub<Qt, 4>(c, d, op_side(op), fz, pm); break;
             case 8: op_rsub<Qt, 8>(c, d, op_side(op), fz, pm); break;
             default: op_rsub<Qt, 8>(c, d, op_side(op), fz, pm); break;  // host emits S <= 8
+            }
+            break;
+        }
+        case OP_RSUB2: {
+            const uint32_t fz = op >> 16;
+            switch (c.N >> d) {
+            case 4: op_rsub2<Qt, 2>(c, d, op_side(op), fz, pm); break;
+            case 8: op_rsub2<Qt, 4>(c, d, op_side(op), fz, pm); break;
+            default: op_rsub2<Qt, 8>(c, d, op_side(op), fz, pm); break;  // host emits 2H <= 16
             }
             break;
         }
