@@ -331,6 +331,28 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, i
     return PSCL_OK;
 }
 
+// Peephole fusion of the schedule: a right register-subtree pair directly
+// followed by its parent's h step takes that step over.
+static void fuse_ops(std::vector<uint32_t> &ops)
+{
+    std::vector<uint32_t> out;
+    out.reserve(ops.size());
+    for (size_t i = 0; i < ops.size(); i++) {
+        const uint32_t a = ops[i];
+        if (i + 1 < ops.size()) {
+            const uint32_t b = ops[i + 1];
+            if (op_code(a) == OP_RSUB2 && op_side(a) == 1 && op_code(b) == OP_COMB &&
+                op_depth(b) == op_depth(a)) {
+                out.push_back(a | ((1u | ((uint32_t)op_side(b) << 1)) << 12));
+                i++;
+                continue;
+            }
+        }
+        out.push_back(a);
+    }
+    ops.swap(out);
+}
+
 static std::vector<int> prune_key(const pscl_pruning *pr, int fuse)
 {
     if (!pr || pr->mask == 0) return {fuse, 0};
@@ -366,6 +388,7 @@ static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, Program *o
     int max_depth = 0;
     rc = gen_program(c, eff, fuse, 0, 0, c->N, 1, ops, max_depth);
     if (rc) return rc;
+    fuse_ops(ops);
     Program p;
     p.n_ops = (int)ops.size();
     p.max_depth = max_depth;

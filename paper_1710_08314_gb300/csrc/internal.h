@@ -24,7 +24,9 @@ enum Opcode : uint32_t {
     OP_RSUB2 = 5, // unpruned subtree of 2H leaves (H = 2..8) at depth d: f,
                   //   left half in registers, g, right half in registers, h;
                   //   the node's LLRs are read twice from layer d and its
-                  //   children's LLRs never reach memory; bits 16..31 as above
+                  //   children's LLRs never reach memory; bits 16..31 as above;
+                  //   t = 1 | parent side << 1: the node is a right child and
+                  //   the parent's h step (OP_COMB) is folded in
 };
 enum NodeType : uint32_t { NT_R0 = 1, NT_R1 = 2, NT_REP = 3, NT_SPC = 4 };
 

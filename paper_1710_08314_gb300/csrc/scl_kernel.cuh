@@ -990,7 +990,7 @@ __device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, ty
 // the h step, with the left half's partial sums following the path through
 // the right half's selections.  Equivalent to F, RSUB, G, RSUB, COMB.
 template <class Qt, int H>
-__device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, uint32_t fz, typename Qt::V &pm)
+__device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, int comb, uint32_t fz, typename Qt::V &pm)
 {
     typedef typename Qt::V V;
     constexpr int S = 2 * H;
@@ -1028,8 +1028,20 @@ __device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, uint32_t fz, t
         else br = beta;
     }
     constexpr uint32_t m = (1u << H) - 1u;
+    const uint32_t beta = ((bl ^ br) & m) | ((br & m) << H);
+    if (comb & 1) {
+        // right child: the parent's h step with the left sibling's partial
+        // sums (BL_d, the column the path holds), into BL/BR_{d-1}
+        constexpr uint32_t m2 = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
+        const int psd = comb >> 1;
+        const uint32_t sib = ld(c, bl_layer(c, d), c.seg + tab_get(c.idxS, d), c.P->lay.b_words[d], 8u);
+        uint32_t *dst = psd == 0 ? bl_layer(c, d - 1) : br_layer(c, d - 1);
+        st(c, dst, c.lane, c.P->lay.b_words[d - 1], ((sib ^ beta) & m2) | ((beta & m2) << S), 16u);
+        if (psd == 0) tab_set(c.idxS, d - 1, c.slot);
+        return;
+    }
     uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
-    st(c, dst, c.lane, c.P->lay.b_words[d], ((bl ^ br) & m) | ((br & m) << H), 64u);
+    st(c, dst, c.lane, c.P->lay.b_words[d], beta, 64u);
     if (side == 0) tab_set(c.idxS, d, c.slot);
 }
 
@@ -1178,9 +1190,9 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         case OP_RSUB2: {
             const uint32_t fz = op >> 16;
             switch (c.N >> d) {
-            case 4: op_rsub2<Qt, 2>(c, d, op_side(op), fz, pm); break;
-            case 8: op_rsub2<Qt, 4>(c, d, op_side(op), fz, pm); break;
-            default: op_rsub2<Qt, 8>(c, d, op_side(op), fz, pm); break;  // host emits 2H <= 16
+            case 4: op_rsub2<Qt, 2>(c, d, op_side(op), op_t(op), fz, pm); break;
+            case 8: op_rsub2<Qt, 4>(c, d, op_side(op), op_t(op), fz, pm); break;
+            default: op_rsub2<Qt, 8>(c, d, op_side(op), op_t(op), fz, pm); break;  // host emits 2H <= 16
             }
             break;
         }
