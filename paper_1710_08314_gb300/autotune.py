@@ -20,7 +20,7 @@ from . import polarscl as ps
 
 DEFAULT_CACHE = os.environ.get(
     "PSCL_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json"))
-WARPS_GRID = (8, 12, 16, 20)
+WARPS_GRID = (8, 12, 16, 20, 24, 28)
 FUSE_GRID = (2, 4, 8)
 _lock = threading.Lock()
 

@@ -536,6 +536,7 @@ struct Plan {
     int n_stages = 0;
     int stages[8];
     size_t budget = 0;         // shared-memory bytes per warp
+    int kv = KV_PLAIN;         // decoder kernel variant
 };
 
 static const int kWarpsPerBlock = 4;
@@ -588,7 +589,8 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     }
     pl->smem_block = (size_t)max_smem * kWarpsPerBlock;
     int bps = 0;
-    cudaError_t e = scl_func_attrs((int)quant, pl->pg.has_nodes != 0, pl->smem_block, 32 * kWarpsPerBlock, &bps);
+    pl->kv = kernel_variant(pl->pg.has_nodes != 0, wps);
+    cudaError_t e = scl_func_attrs((int)quant, pl->kv, pl->smem_block, 32 * kWarpsPerBlock, &bps);
     if (e != cudaSuccess) return fail(PSCL_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     if (bps < 1) return fail(PSCL_EUNSUPPORTED, "no block fits (shared memory %zu bytes)", pl->smem_block);
     const int max_warps = dp.sms * bps * kWarpsPerBlock;
@@ -620,11 +622,11 @@ extern "C" int pscl_workspace_size(pscl_code c, int n_frames, int L, pscl_algo a
     return PSCL_OK;
 }
 
-static cudaError_t launch_stage(int quant, bool nodes, const KParams &kp, int grid, size_t smem, cudaStream_t s)
+static cudaError_t launch_stage(int quant, int kv, const KParams &kp, int grid, size_t smem, cudaStream_t s)
 {
-    if (quant == PSCL_F32) return launch_scl_f32(kp, nodes, grid, 32 * kWarpsPerBlock, smem, s);
-    if (quant == PSCL_I16) return launch_scl_i16(kp, nodes, grid, 32 * kWarpsPerBlock, smem, s);
-    return launch_scl_i8(kp, nodes, grid, 32 * kWarpsPerBlock, smem, s);
+    if (quant == PSCL_F32) return launch_scl_f32(kp, kv, grid, 32 * kWarpsPerBlock, smem, s);
+    if (quant == PSCL_I16) return launch_scl_i16(kp, kv, grid, 32 * kWarpsPerBlock, smem, s);
+    return launch_scl_i8(kp, kv, grid, 32 * kWarpsPerBlock, smem, s);
 }
 
 static int g_last_launches = 0;
@@ -678,7 +680,7 @@ static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_a
             CU(cudaMemsetAsync(it.next_count, 0, sizeof(int32_t), stream));
         }
         const size_t smem = (size_t)it.lay.smem_per_warp * kWarpsPerBlock;
-        cudaError_t e = launch_stage((int)quant, pl.pg.has_nodes != 0, kp, pl.grid, smem, stream);
+        cudaError_t e = launch_stage((int)quant, pl.kv, kp, pl.grid, smem, stream);
         if (e != cudaSuccess) return fail(PSCL_ECUDA, "decode launch: %s", cudaGetErrorString(e));
         launches++;
     }
@@ -866,6 +868,7 @@ extern "C" int pscl_decode_static(pscl_code c, const float *llr, int n_frames, i
 struct BatchGroup {
     int quant = 0;
     bool nodes = false;
+    int kv = KV_PLAIN;
     int n_tasks = 0;
     int grid = 0;
     int total_warps = 0;
@@ -979,7 +982,8 @@ extern "C" int pscl_batch_create(const pscl_work_item *items, int n_items, pscl_
         g.n_tasks = (int)h_tasks.size();
         g.smem_block = (size_t)g.smem_per_warp * kWarpsPerBlock;
         int bps = 0;
-        e = scl_func_attrs(q, g.nodes, g.smem_block, 32 * kWarpsPerBlock, &bps);
+        g.kv = kernel_variant(g.nodes, g_target_warps_per_sm);
+        e = scl_func_attrs(q, g.kv, g.smem_block, 32 * kWarpsPerBlock, &bps);
         if (e != cudaSuccess || bps < 1) {
             batch_free(b);
             return fail(PSCL_EUNSUPPORTED, "batch: no block fits (%zu bytes of shared memory)", g.smem_block);
@@ -1053,7 +1057,7 @@ extern "C" int pscl_batch_run(pscl_batch b, const float *llr_pool, uint8_t *info
         kp.info_pool = info_pool;
         kp.status_pool = status_pool;
         CU(cudaMemsetAsync(g.d_ctr, 0, sizeof(int), s));
-        cudaError_t e = launch_stage(g.quant, g.nodes, kp, g.grid, g.smem_block, s);
+        cudaError_t e = launch_stage(g.quant, g.kv, kp, g.grid, g.smem_block, s);
         if (e != cudaSuccess) return fail(PSCL_ECUDA, "batch launch: %s", cudaGetErrorString(e));
         launches++;
     }
@@ -1088,7 +1092,7 @@ extern "C" int pscl_batch_run_plain(pscl_batch b, const float *llr_pool, uint8_t
             kp.gmem_per_warp = g.gmem_per_warp;
             kp.smem_per_warp = kp.single.lay.smem_per_warp;
             kp.total_warps = grid * kWarpsPerBlock;
-            cudaError_t e = launch_stage(g.quant, g.nodes, kp, grid, (size_t)kp.smem_per_warp * kWarpsPerBlock, s);
+            cudaError_t e = launch_stage(g.quant, g.kv, kp, grid, (size_t)kp.smem_per_warp * kWarpsPerBlock, s);
             if (e != cudaSuccess) return fail(PSCL_ECUDA, "plain launch: %s", cudaGetErrorString(e));
             launches++;
         }

@@ -117,10 +117,18 @@ struct KParams {
 
 // launchers, one per number format (defined in scl_*.cu)
 // nodes: the schedule contains pruned nodes (R0/R1/REP/SPC steps)
-cudaError_t launch_scl_f32(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_scl_i16(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_scl_i8(const KParams &p, bool nodes, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t scl_func_attrs(int quant, bool nodes, size_t smem, int block, int *blocks_per_sm);
+// decoder kernel variants: node-free with 5 blocks of 4 warps per SM (96
+// registers), node-capable (4 blocks), node-free with 7 blocks (72 registers,
+// for tunings of 24 or more resident warps per SM)
+enum KernelVariant : int { KV_PLAIN = 0, KV_NODES = 1, KV_DENSE = 2 };
+inline int kernel_variant(bool nodes, int warps_per_sm)
+{
+    return nodes ? KV_NODES : (warps_per_sm >= 24 ? KV_DENSE : KV_PLAIN);
+}
+cudaError_t launch_scl_f32(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_scl_i16(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_scl_i8(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t scl_func_attrs(int quant, int kv, size_t smem, int block, int *blocks_per_sm);
 
 // ---------------------------------------------------------------------------
 // serving loop (server.cu)

@@ -1300,9 +1300,10 @@ __device__ __forceinline__ void load_item(Ctx &c, const Item *src, const KParams
 // (uneven batches) the next task comes from a device counter, so warps that
 // drew short frames take more of them; otherwise warps stride over the
 // frames of the single item.
-// the node-free variant fits five blocks of four warps per SM (<= 102 registers)
-template <class Qt, bool NODES>
-__global__ void __launch_bounds__(128, NODES ? 4 : 5) scl_kernel(const __grid_constant__ KParams K)
+// MINB blocks of four warps per SM bound the registers: the node-capable
+// variant runs 4 (128 registers), the node-free one 5 (96) or 7 (72)
+template <class Qt, bool NODES, int MINB>
+__global__ void __launch_bounds__(128, MINB) scl_kernel(const __grid_constant__ KParams K)
 {
     extern __shared__ __align__(16) char smem[];
     Ctx c;
