@@ -179,15 +179,39 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
                 syn[(size_t)q * 256 + v] = e;
             }
     }
+    // info-bit extraction per codeword byte: the byte's info positions (A
+    // indices below K_info, increasing) are consecutive bits of the output
+    std::vector<uint8_t> ext((size_t)NB * 256, 0);
+    std::vector<uint16_t> ext_pos((size_t)NB + 1, 0);
+    {
+        std::vector<uint8_t> info_pos(N, 0);
+        for (int k = 0; k < c->kinfo; ++k) info_pos[A[k]] = 1;
+        int k = 0;
+        for (int q = 0; q < NB; ++q) {
+            ext_pos[q] = (uint16_t)k;
+            for (int v = 0; v < 256; ++v) {
+                uint32_t o = 0;
+                int j = 0;
+                for (int b = 0; b < 8; ++b)
+                    if (info_pos[8 * q + b]) o |= (uint32_t)((v >> b) & 1) << j++;
+                ext[(size_t)q * 256 + v] = (uint8_t)o;
+            }
+            for (int b = 0; b < 8; ++b) k += info_pos[8 * q + b];
+        }
+        ext_pos[NB] = (uint16_t)k;
+    }
     size_t off_in = 0, off_A = off_in + 4 * (size_t)N, off_am = off_A + ((2 * (size_t)K + 15) & ~(size_t)15),
            off_lut = off_am + ((4 * (size_t)NW + 15) & ~(size_t)15), off_syn = off_lut + 1024,
-           total = off_syn + 4 * syn.size();
+           off_ext = off_syn + 4 * syn.size(), off_epos = off_ext + ext.size(),
+           total = off_epos + ((2 * ext_pos.size() + 15) & ~(size_t)15);
     std::vector<uint8_t> blob(total, 0);
     memcpy(blob.data() + off_in, in_index.data(), 4 * (size_t)N);
     memcpy(blob.data() + off_A, A.data(), 2 * (size_t)K);
     memcpy(blob.data() + off_am, amask.data(), 4 * (size_t)NW);
     memcpy(blob.data() + off_lut, lut.data(), 1024);
     memcpy(blob.data() + off_syn, syn.data(), 4 * syn.size());
+    memcpy(blob.data() + off_ext, ext.data(), ext.size());
+    memcpy(blob.data() + off_epos, ext_pos.data(), 2 * ext_pos.size());
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_blob, total);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), total, cudaMemcpyHostToDevice);
@@ -212,6 +236,8 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
     dc.amask = (const uint32_t *)(base + off_am);
     dc.crc_lut = (const uint32_t *)(base + off_lut);
     dc.syn = (const uint32_t *)(base + off_syn);
+    dc.ext = (const uint8_t *)(base + off_ext);
+    dc.ext_pos = (const uint16_t *)(base + off_epos);
     *out = c;
     return PSCL_OK;
 }

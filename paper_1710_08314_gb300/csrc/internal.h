@@ -50,6 +50,8 @@ struct DevCode {
     const uint32_t *amask;      // max(1, N/32) words: bit set for positions in A
     const uint32_t *crc_lut;    // 256 entries, MSB-first table for the 32-bit-aligned CRC
     const uint32_t *syn;        // N/8 x 256: CRC syndrome contribution of codeword byte q with value v
+    const uint8_t *ext;         // N/8 x 256: the info bits of codeword byte q with value v, packed LSB first
+    const uint16_t *ext_pos;    // N/8 + 1: index of the first info bit of codeword byte q in u_A
 };
 
 // Per-warp memory map.  Offsets are bytes inside the warp's shared-memory

@@ -1136,9 +1136,11 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     int32_t *fids = (int32_t *)(c.sm + P.lay.src_off) + 64;  // 32 frame ids
     // frame id of this lane's frame (-1: none)
     const int pos = pos0 + c.fiw;
-    int frame = -1;
-    if (pos < count) frame = P.frame_list ? __ldg(&P.frame_list[pos]) : pos;
-    if (c.slot == 0) fids[c.fiw] = frame;
+    {
+        int frame = -1;
+        if (pos < count) frame = P.frame_list ? __ldg(&P.frame_list[pos]) : pos;
+        if (c.slot == 0) fids[c.fiw] = frame;
+    }
     __syncwarp();
     // layer 0: channel LLRs of the warp's frames, quantised and packed
     {
@@ -1220,6 +1222,9 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     const bool wok = ((key >> 40) & 1u) == 0;
     const int wcol = c.seg + win;
     const int wcl = __shfl_sync(PSCL_FULL, cl, wcol);
+    // frame ids from shared memory (not kept in registers across the walk)
+    const int32_t *fid = (const int32_t *)(c.sm + P.lay.src_off) + 64;
+    const int frame = fid[c.fiw];
     if (frame >= 0) {
         if (c.slot == 0) {
             bool pass = wok;
@@ -1234,22 +1239,44 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
                 P.pm_out[(size_t)frame * (size_t)P.L_out + s] = (s == c.slot && active) ? Qt::to_float(pm)
                                                                                         : __uint_as_float(0x7F800000u);
         }
-        const int nbytes = (cd.kinfo + 7) >> 3;
-        for (int b = c.slot; b < nbytes; b += c.L) {
-            uint32_t byte = 0, wv = 0;
-            int cw = -1;  // positions increase: reload only when the word changes
-            for (int k = 0; k < 8; ++k) {
-                const int i = 8 * b + k;
-                if (i < cd.kinfo) {
-                    const int pz = __ldg(&cd.A[i]);
-                    if ((pz >> 5) != cw) {
-                        cw = pz >> 5;
-                        wv = uword(c, cw, wcol, wcl);
+    }
+    // info bits of each frame's winning path, the whole warp on one frame at
+    // a time: a lane takes four codeword bytes per step, looks up their info
+    // bits (table per byte) and ORs them into a bit buffer in shared memory
+    // (u_A order, LSB first in 32-bit words); then the lanes write the bytes
+    // out MSB first.
+    const int nbytes = (cd.kinfo + 7) >> 3;
+    const int NB = c.N >> 3;
+    uint32_t *buf = (uint32_t *)(c.sm + P.lay.src_off);  // 64 words: K_info <= 2048
+    for (int f = 0; f < c.fpw; ++f) {
+        const int fr = fid[f];
+        const int wc = __shfl_sync(PSCL_FULL, wcol, f * c.L);
+        const int wl = __shfl_sync(PSCL_FULL, wcl, f * c.L);
+        if (fr < 0) continue;  // warp-uniform
+        __syncwarp();
+        buf[c.lane] = 0u;
+        buf[c.lane + 32] = 0u;
+        __syncwarp();
+        for (int q0 = 4 * c.lane; q0 < NB; q0 += 128) {
+            const uint32_t x = uword(c, q0 >> 2, wc, wl);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = q0 + j;
+                if (q < NB) {
+                    const int k = __ldg(&cd.ext_pos[q]);
+                    const int cnt = __ldg(&cd.ext_pos[q + 1]) - k;
+                    if (cnt > 0) {
+                        const uint32_t v = __ldg(&cd.ext[(q << 8) | ((x >> (8 * j)) & 0xFFu)]);
+                        atomicOr(&buf[k >> 5], v << (k & 31));
+                        if ((k & 31) + cnt > 32) atomicOr(&buf[(k >> 5) + 1], v >> (32 - (k & 31)));
                     }
-                    byte |= ((wv >> (pz & 31)) & 1u) << (7 - k);
                 }
             }
-            P.info_out[(size_t)frame * (size_t)nbytes + b] = (uint8_t)byte;
+        }
+        __syncwarp();
+        for (int b = c.lane; b < nbytes; b += 32) {
+            const uint32_t byte = (buf[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+            P.info_out[(size_t)fr * (size_t)nbytes + b] = (uint8_t)(__brev(byte) >> 24);
         }
     }
     __syncwarp();
