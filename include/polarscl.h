@@ -112,7 +112,7 @@ int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
  * else = the pruned entry): warps_per_sm (1..32) sizes each warp's shared-memory
  * slice (more warps hide more latency, fewer keep more LLR layers on chip);
  * fuse_leaves (1, 2, 4, 8) is the largest unpruned subtree decoded in
- * registers.  (0, 0) restores the defaults (20 warps, 8 leaves).  Results
+ * registers.  (0, 0) restores the defaults (28 warps, 8 leaves).  Results
  * never depend on the tuning.  Written by the package's autotuner.         */
 int pscl_code_tune(pscl_code code, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
                    int fuse_leaves);
@@ -281,6 +281,27 @@ int pscl_server_status(pscl_server s, int *running, int *device_status, uint64_t
 /* Raise the abort word and wait (at most timeout_ms) for the kernel to end,
  * then free everything; PSCL_ETIMEDOUT keeps the resources.                 */
 int pscl_server_stop(pscl_server s, int timeout_ms);
+
+/* Process-wide defaults, used where a code has no pscl_code_tune entry and
+ * by every batch and server (no counterpart in the paper: GPU scheduling).
+ * pscl_set_tuning: resident warps per SM the shared-memory slices are sized
+ *   for, 1..64 (default 28); 24 and more select the 72-register decoder
+ *   variant for schedules without pruned nodes.
+ * pscl_set_fusion: largest register subtree, 1, 2, 4 or 8 leaves (default 8;
+ *   1 = none).  Not thread-safe against concurrent decodes; results never
+ *   depend on either.  PSCL_EINVAL outside the ranges.                      */
+int pscl_set_tuning(int target_warps_per_sm);
+int pscl_set_fusion(int max_leaves);
+
+/* Test hooks.  pscl_debug_last_launches: kernel launches of the calling
+ * process's most recent decode or batch run.  pscl_debug_error_word: the
+ * bounds-check word of the current device's library workspace (non-zero only
+ * in the checked build, after an out-of-range access was caught and
+ * skipped); *out = 0 when no workspace exists.  pscl_debug_checked: 1 in
+ * the checked build, else 0.                                                */
+int pscl_debug_last_launches(void);
+int pscl_debug_error_word(uint32_t *out);
+int pscl_debug_checked(void);
 
 /* Message for the calling thread's most recent error ("" if none).         */
 const char *pscl_last_error(void);

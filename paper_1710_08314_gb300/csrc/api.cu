@@ -54,6 +54,7 @@ struct DevProps {
     int sms = 0;
     int smem_optin = 0;
     int smem_per_sm = 0;
+    int smem_reserved = 0;  // per block, taken by the runtime
 };
 static std::mutex g_mu;
 static std::map<int, DevProps> g_props;
@@ -69,6 +70,7 @@ static int get_props(DevProps *out)
         CU(cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev));
         CU(cudaDeviceGetAttribute(&p.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         CU(cudaDeviceGetAttribute(&p.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        CU(cudaDeviceGetAttribute(&p.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
         it = g_props.emplace(dev, p).first;
     }
     *out = it->second;
@@ -286,7 +288,7 @@ static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
 // shared-memory slice is sized for; per code and (L, format) the autotuner's
 // measurements override them (pscl_code_tune)
 static int g_fuse_max = 8;
-static int g_target_warps_per_sm = 20;
+static int g_target_warps_per_sm = 28;
 
 static int tune_key(int L, int quant, const pscl_pruning *pr)
 {
@@ -567,6 +569,17 @@ struct Plan {
 
 static const int kWarpsPerBlock = 4;
 
+// shared-memory bytes per warp when wps warps (in blocks of four) share an
+// SM: what is left after the runtime's per-block reservation, evenly split
+static size_t slice_budget(const DevProps &dp, int wps)
+{
+    const int blocks = (wps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const long long usable = (long long)dp.smem_per_sm - (long long)blocks * dp.smem_reserved;
+    size_t budget = usable > 0 ? (size_t)usable / (size_t)(blocks * kWarpsPerBlock) : 0;
+    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    return budget & ~(size_t)15;
+}
+
 static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const pscl_pruning *pr, pscl_quant quant,
                      Plan *pl, bool build_program = true)
 {
@@ -601,9 +614,7 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     // every stage uses the same per-warp slices (the layout of the smallest
     // list size needs the most layer-0 room, the largest the most paths:
     // both only depend on N, EPW and 32/L for layer 0)
-    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
-    size_t budget = per_sm / (size_t)wps;
-    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    const size_t budget = slice_budget(dp, wps);
     pl->budget = budget;
     // each stage recomputes its own layout at launch; the plan keeps maxima
     uint32_t max_smem = 0, max_gmem = 0;
@@ -964,9 +975,7 @@ extern "C" int pscl_batch_create(const pscl_work_item *items, int n_items, pscl_
     b->allocs.push_back(p);
     b->d_err = (uint32_t *)p;
     cudaMemset(p, 0, 256);
-    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
-    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
-    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    const size_t budget = slice_budget(dp, g_target_warps_per_sm);
     for (int q = PSCL_F32; q <= PSCL_I8; q++) {
         BatchGroup g;
         g.quant = q;
@@ -1209,9 +1218,9 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
     s->R = R;
     s->max_frames = cfg->max_frames_per_request;
     s->max_inflight = cfg->max_inflight_frames > 0 ? cfg->max_inflight_frames : (long long)R * cfg->max_frames_per_request;
-    const size_t per_sm = (size_t)dp.smem_per_sm - 1024 * 2;
-    size_t budget = per_sm / (size_t)g_target_warps_per_sm;
-    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    // the serving kernel keeps 4 blocks of 4 warps per SM (its registers):
+    // slices are sized for at most that many
+    const size_t budget = slice_budget(dp, g_target_warps_per_sm < 16 ? g_target_warps_per_sm : 16);
     uint32_t smem_pw = 0, gmem_pw = 0;
     s->h_items.resize((size_t)cfg->n_contexts);
     for (int i = 0; i < cfg->n_contexts; i++) {
