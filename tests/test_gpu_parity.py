@@ -23,11 +23,12 @@ def prunes(kind):
     return pruning(**p), oracle.pruning(**p)
 
 
-def run_case(name, n, ebn0, L, algo, quant, prune_kind, seed, systematic=True, frames=None):
+def run_case(name, n, ebn0, L, algo, quant, prune_kind, seed, systematic=True, frames=None, gcode=None):
     d = synth.load_code(name)
     code, info, llr = make_inputs(d, n, ebn0, seed, systematic)
     gp, op = prunes(prune_kind)
-    gcode = gpu_code(d, systematic)
+    if gcode is None:
+        gcode = gpu_code(d, systematic)
     g = gpu_decode(gcode, llr, L, algo, quant, gp)
     sub = llr if frames is None else llr[frames]
     o = oracle_decode(code, sub, L, algo, quant, op)
@@ -77,6 +78,23 @@ def test_n2048_l32_sampled_frames():
     frames = np.array([0, 1, 777, 2047])
     run_case("c2_2048_1723", 2048, 3.5, 32, "cascl", "f32", None, 11, frames=frames)
     run_case("c2_2048_1723", 2048, 3.5, 32, "fascl", "i8", "i8", 12, frames=frames)
+
+
+@pytest.mark.parametrize("quant,fuse", [("f32", 4), ("i8", 2)])
+def test_benchmark_launch_configuration_sampled_frames(quant, fuse):
+    # the headline launch: 16384 frames at 4.5 dB, 28 warps per SM (the
+    # 72-register kernel variant), the benchmark's fusion size; sampled frames
+    # against the oracle, and nearly every frame must pass its CRC at this
+    # SNR (a scratch mix-up between warps would corrupt many)
+    from paper_1710_08314_gb300 import polarscl as ps
+    from gpu_helpers import QMAP
+    d = synth.load_code("c2_2048_1723")
+    gcode = gpu_code(d)
+    ps.pscl_code_tune(gcode.handle, 32, QMAP[quant][0], 28, fuse, None)
+    frames = np.array([0, 4095, 9001, 16383])
+    g, info = run_case("c2_2048_1723", 16384, 4.5, 32, "cascl", quant, None, 13, frames=frames, gcode=gcode)
+    fails = int(((g[1] & 1) == 0).sum())
+    assert fails <= 16, f"{fails} of 16384 frames failed their CRC at 4.5 dB"
 
 
 def test_tiny_codes_and_edge_shapes():
