@@ -591,6 +591,89 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
     newkey = e1;
 }
 
+// The general case of select_m2: the L-th smallest metric value is found
+// (float: 32-bit bitonic network of the 2L patterns; fixed point: bisection on
+// the metric's bits with ballot counts) and ties at that value are resolved in
+// candidate order; the survivors are scattered through shared memory (src, 64
+// words) into their new slots.  Returns (key << 32) | (parent slot << 8) |
+// candidate.  The node-capable kernel calls it out of line (its register
+// pressure is highest around the node handlers).
+template <int VBITS>
+__device__ __forceinline__ uint64_t select_m2_general(uint32_t a, uint32_t b, uint32_t ka, uint32_t kb, int L,
+                                                      int lane, int slot, int seg, uint32_t *src)
+{
+    const uint32_t segmask = L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << seg);
+    uint32_t tau;
+    if constexpr (VBITS > 0) {
+        // fixed point: metrics are integers below 2^VBITS, so the L-th
+        // smallest value is found by bisection on its bits (ballot counts)
+        uint32_t v = 0;
+#pragma unroll
+        for (int bit = VBITS - 1; bit >= 0; --bit) {
+            const uint32_t cand = v | ((1u << bit) - 1u);
+            const int cnt = __popc(__ballot_sync(PSCL_FULL, a <= cand) & segmask) +
+                            __popc(__ballot_sync(PSCL_FULL, b <= cand) & segmask);
+            if (cnt < L) v |= 1u << bit;
+        }
+        tau = v;
+    } else {
+        // float: bitonic sort of the 2L metric patterns, element e = 2*slot + m
+        uint32_t k0 = a, k1 = b;
+        for (int size = 2; size <= 2 * L; size <<= 1) {
+            const bool up = ((slot << 1) & size) == 0;
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                if (stride == 1) {
+                    const uint32_t lo = min(k0, k1), hi = max(k0, k1);
+                    k0 = up ? lo : hi;
+                    k1 = up ? hi : lo;
+                } else {
+                    const int ls = stride >> 1;
+                    const bool takemin = ((slot & ls) == 0) == up;
+                    const uint32_t o0 = __shfl_xor_sync(PSCL_FULL, k0, ls);
+                    const uint32_t o1 = __shfl_xor_sync(PSCL_FULL, k1, ls);
+                    k0 = takemin ? min(k0, o0) : max(k0, o0);
+                    k1 = takemin ? min(k1, o1) : max(k1, o1);
+                }
+            }
+        }
+        const int tp = (L - 1) >> 1;
+        const uint32_t tsel = ((L - 1) & 1) ? k1 : k0;
+        tau = __shfl_sync(PSCL_FULL, tsel, seg + tp);
+    }
+    const uint32_t lt = ((1u << lane) - 1u) & segmask;
+    const uint32_t BA = __ballot_sync(PSCL_FULL, a < tau) & segmask;
+    const uint32_t BB = __ballot_sync(PSCL_FULL, b < tau) & segmask;
+    const uint32_t EA = __ballot_sync(PSCL_FULL, a == tau) & segmask;
+    const uint32_t EB = __ballot_sync(PSCL_FULL, b == tau) & segmask;
+    const int need = L - __popc(BA) - __popc(BB);
+    const int ra = __popc(EA & lt) + __popc(EB & lt);
+    const bool sa = a < tau || (a == tau && ra < need);
+    const int rb = ra + (a == tau ? 1 : 0);
+    const bool sb = b < tau || (b == tau && rb < need);
+    const uint32_t SA = __ballot_sync(PSCL_FULL, sa) & segmask;
+    const uint32_t SB = __ballot_sync(PSCL_FULL, sb) & segmask;
+    int r = __popc(SA & lt) + __popc(SB & lt);
+    if (sa) {
+        src[2 * (seg + r)] = (uint32_t)slot << 8;
+        src[2 * (seg + r) + 1] = ka;
+        ++r;
+    }
+    if (sb) {
+        src[2 * (seg + r)] = ((uint32_t)slot << 8) | 1u;
+        src[2 * (seg + r) + 1] = kb;
+    }
+    __syncwarp();
+    const uint32_t e0 = src[2 * lane], e1 = src[2 * lane + 1];
+    __syncwarp();
+    return ((uint64_t)e1 << 32) | e0;
+}
+template <int VBITS>
+__device__ __noinline__ uint64_t select_m2_general_call(uint32_t a, uint32_t b, uint32_t ka, uint32_t kb, int L,
+                                                        int lane, int slot, int seg, uint32_t *src)
+{
+    return select_m2_general<VBITS>(a, b, ka, kb, L, lane, slot, seg, src);
+}
+
 // Two candidates per path (an information leaf, or a REP node): candidate
 // (p, 0) has metric key ka, (p, 1) key kb, candidate ids c = 2p and 2p + 1.
 // Same result as select_paths<2>: the L smallest (PM, c) survive and take new
@@ -598,7 +681,7 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
 // every first candidate, the first candidates are the survivors and no sort
 // is needed; otherwise the L-th smallest metric value is found with a 32-bit
 // bitonic network and ties at that value are resolved in candidate order.
-template <int VBITS>
+template <int VBITS, bool OUT>
 __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int &par, int &cand,
                                           uint32_t &newkey, int &n_keep, bool &ident)
 {
@@ -632,70 +715,10 @@ __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int 
             return;
         }
     }
-    const uint32_t segmask = L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << c.seg);
-    uint32_t tau;
-    if constexpr (VBITS > 0) {
-        // fixed point: metrics are integers below 2^VBITS, so the L-th
-        // smallest value is found by bisection on its bits (ballot counts)
-        uint32_t v = 0;
-#pragma unroll
-        for (int bit = VBITS - 1; bit >= 0; --bit) {
-            const uint32_t cand = v | ((1u << bit) - 1u);
-            const int cnt = __popc(__ballot_sync(PSCL_FULL, a <= cand) & segmask) +
-                            __popc(__ballot_sync(PSCL_FULL, b <= cand) & segmask);
-            if (cnt < L) v |= 1u << bit;
-        }
-        tau = v;
-    } else {
-        // float: bitonic sort of the 2L metric patterns, element e = 2*slot + m
-        uint32_t k0 = a, k1 = b;
-        for (int size = 2; size <= 2 * L; size <<= 1) {
-            const bool up = ((c.slot << 1) & size) == 0;
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                if (stride == 1) {
-                    const uint32_t lo = min(k0, k1), hi = max(k0, k1);
-                    k0 = up ? lo : hi;
-                    k1 = up ? hi : lo;
-                } else {
-                    const int ls = stride >> 1;
-                    const bool takemin = ((c.slot & ls) == 0) == up;
-                    const uint32_t o0 = __shfl_xor_sync(PSCL_FULL, k0, ls);
-                    const uint32_t o1 = __shfl_xor_sync(PSCL_FULL, k1, ls);
-                    k0 = takemin ? min(k0, o0) : max(k0, o0);
-                    k1 = takemin ? min(k1, o1) : max(k1, o1);
-                }
-            }
-        }
-        const int tp = (L - 1) >> 1;
-        const uint32_t tsel = ((L - 1) & 1) ? k1 : k0;
-        tau = __shfl_sync(PSCL_FULL, tsel, c.seg + tp);
-    }
-    const uint32_t lt = ((1u << c.lane) - 1u) & segmask;
-    const uint32_t BA = __ballot_sync(PSCL_FULL, a < tau) & segmask;
-    const uint32_t BB = __ballot_sync(PSCL_FULL, b < tau) & segmask;
-    const uint32_t EA = __ballot_sync(PSCL_FULL, a == tau) & segmask;
-    const uint32_t EB = __ballot_sync(PSCL_FULL, b == tau) & segmask;
-    const int need = L - __popc(BA) - __popc(BB);
-    const int ra = __popc(EA & lt) + __popc(EB & lt);
-    const bool sa = a < tau || (a == tau && ra < need);
-    const int rb = ra + (a == tau ? 1 : 0);
-    const bool sb = b < tau || (b == tau && rb < need);
-    const uint32_t SA = __ballot_sync(PSCL_FULL, sa) & segmask;
-    const uint32_t SB = __ballot_sync(PSCL_FULL, sb) & segmask;
-    int r = __popc(SA & lt) + __popc(SB & lt);
     uint32_t *src = (uint32_t *)(c.sm + c.P->lay.src_off);
-    if (sa) {
-        src[2 * (c.seg + r)] = (uint32_t)c.slot << 8;
-        src[2 * (c.seg + r) + 1] = ka;
-        ++r;
-    }
-    if (sb) {
-        src[2 * (c.seg + r)] = ((uint32_t)c.slot << 8) | 1u;
-        src[2 * (c.seg + r) + 1] = kb;
-    }
-    __syncwarp();
-    const uint32_t e0 = src[2 * c.lane], e1 = src[2 * c.lane + 1];
-    __syncwarp();
+    const uint64_t r = OUT ? select_m2_general_call<VBITS>(a, b, ka, kb, L, c.lane, c.slot, c.seg, src)
+                           : select_m2_general<VBITS>(a, b, ka, kb, L, c.lane, c.slot, c.seg, src);
+    const uint32_t e0 = (uint32_t)r, e1 = (uint32_t)(r >> 32);
     par = (int)(e0 >> 8) & (L - 1);
     cand = (int)(e0 & 1u);
     newkey = e1;
@@ -715,7 +738,7 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
     int par, cand, n_keep;
     uint32_t newkey;
     bool ident;
-    if constexpr (M == 2) select_m2<Qt::VBITS>(c, kp[0], kp[1], par, cand, newkey, n_keep, ident);
+    if constexpr (M == 2) select_m2<Qt::VBITS, true>(c, kp[0], kp[1], par, cand, newkey, n_keep, ident);
     else select_paths<M>(c, kp, par, cand, newkey, n_keep, ident);
     const int pl = c.seg + par;
     uint32_t hp = h, r0 = rp[0], r1 = rp[1], r2 = rp[2];
@@ -907,7 +930,7 @@ __device__ __forceinline__ void op_node(Ctx &c, int d, int type, int side, int t
 // parent lane after a selection (the lazy path copy of the register part);
 // when every path keeps its own slot nothing moves.  Returns the node's
 // partial sums (S bits).
-template <class Qt, int S, class Shuf>
+template <class Qt, int S, bool OUT, class Shuf>
 __device__ __forceinline__ uint32_t rsub(Ctx &c, typename Qt::V (&a)[S], uint32_t fz, typename Qt::V &pm,
                                          const Shuf &shuf)
 {
@@ -922,7 +945,7 @@ __device__ __forceinline__ uint32_t rsub(Ctx &c, typename Qt::V (&a)[S], uint32_
         int par, cand, nk;
         uint32_t nkey;
         bool ident;
-        select_m2<Qt::VBITS>(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk, ident);
+        select_m2<Qt::VBITS, OUT>(c, Qt::key(pm), Qt::key(Qt::add(pm, Qt::absv(lam))), par, cand, nkey, nk, ident);
         uint32_t hd = (uint32_t)(lam < 0);
         if (!ident) {
             const int pl = c.seg + par;
@@ -947,7 +970,7 @@ __device__ __forceinline__ uint32_t rsub(Ctx &c, typename Qt::V (&a)[S], uint32_
 #pragma unroll
             for (int i = 0; i < S; ++i) a[i] = __shfl_sync(PSCL_FULL, a[i], pl);
         };
-        uint32_t bl = rsub<Qt, H>(c, l, fz, pm, shuf_l);
+        uint32_t bl = rsub<Qt, H, OUT>(c, l, fz, pm, shuf_l);
         V r[H];
 #pragma unroll
         for (int i = 0; i < H; ++i) r[i] = Qt::g1(a[i], a[i + H], (bl >> i) & 1u);
@@ -955,13 +978,13 @@ __device__ __forceinline__ uint32_t rsub(Ctx &c, typename Qt::V (&a)[S], uint32_
             shuf(pl);
             bl = __shfl_sync(PSCL_FULL, bl, pl);
         };
-        const uint32_t br = rsub<Qt, H>(c, r, fz >> H, pm, shuf_r);
+        const uint32_t br = rsub<Qt, H, OUT>(c, r, fz >> H, pm, shuf_r);
         const uint32_t m = (1u << H) - 1u;
         return ((bl ^ br) & m) | ((br & m) << H);
     }
 }
 
-template <class Qt, int S>
+template <class Qt, int S, bool OUT>
 __device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, typename Qt::V &pm)
 {
     typedef typename Qt::V V;
@@ -978,7 +1001,7 @@ __device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, ty
             if (w * Qt::EPW + e < S) a[w * Qt::EPW + e] = Qt::elem(wd, e);
     }
     auto none = [](int) {};
-    const uint32_t beta = rsub<Qt, S>(c, a, fz, pm, none);
+    const uint32_t beta = rsub<Qt, S, OUT>(c, a, fz, pm, none);
     uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
     st(c, dst, c.lane, c.P->lay.b_words[d], beta, 64u);
     if (side == 0) tab_set(c.idxS, d, c.slot);
@@ -989,7 +1012,7 @@ __device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, ty
 // holds after the left half's selections), the right subtree in registers and
 // the h step, with the left half's partial sums following the path through
 // the right half's selections.  Equivalent to F, RSUB, G, RSUB, COMB.
-template <class Qt, int H>
+template <class Qt, int H, bool OUT>
 __device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, int comb, uint32_t fz, typename Qt::V &pm)
 {
     typedef typename Qt::V V;
@@ -1023,7 +1046,7 @@ __device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, int comb, uint
             const V y = Qt::elem(wd[(i + H) / Qt::EPW], (i + H) % Qt::EPW);
             a[i] = half == 0 ? Qt::f1(x, y) : Qt::g1(x, y, (bl >> i) & 1u);
         }
-        const uint32_t beta = rsub<Qt, H>(c, a, fz >> (half * H), pm, carry);
+        const uint32_t beta = rsub<Qt, H, OUT>(c, a, fz >> (half * H), pm, carry);
         if (half == 0) bl = beta;
         else br = beta;
     }
@@ -1182,19 +1205,19 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         case OP_RSUB: {
             const uint32_t fz = op >> 16;
             switch (c.N >> d) {
-            case 2: op_rsub<Qt, 2>(c, d, op_side(op), fz, pm); break;
-            case 4: op_rsub<Qt, 4>(c, d, op_side(op), fz, pm); break;
-            case 8: op_rsub<Qt, 8>(c, d, op_side(op), fz, pm); break;
-            default: op_rsub<Qt, 8>(c, d, op_side(op), fz, pm); break;  // host emits S <= 8
+            case 2: op_rsub<Qt, 2, NODES>(c, d, op_side(op), fz, pm); break;
+            case 4: op_rsub<Qt, 4, NODES>(c, d, op_side(op), fz, pm); break;
+            case 8: op_rsub<Qt, 8, NODES>(c, d, op_side(op), fz, pm); break;
+            default: op_rsub<Qt, 8, NODES>(c, d, op_side(op), fz, pm); break;  // host emits S <= 8
             }
             break;
         }
         case OP_RSUB2: {
             const uint32_t fz = op >> 16;
             switch (c.N >> d) {
-            case 4: op_rsub2<Qt, 2>(c, d, op_side(op), op_t(op), fz, pm); break;
-            case 8: op_rsub2<Qt, 4>(c, d, op_side(op), op_t(op), fz, pm); break;
-            default: op_rsub2<Qt, 8>(c, d, op_side(op), op_t(op), fz, pm); break;  // host emits 2H <= 16
+            case 4: op_rsub2<Qt, 2, NODES>(c, d, op_side(op), op_t(op), fz, pm); break;
+            case 8: op_rsub2<Qt, 4, NODES>(c, d, op_side(op), op_t(op), fz, pm); break;
+            default: op_rsub2<Qt, 8, NODES>(c, d, op_side(op), op_t(op), fz, pm); break;  // host emits 2H <= 16
             }
             break;
         }
