@@ -14,7 +14,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 
 import numpy as np
 import os
