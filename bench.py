@@ -448,6 +448,35 @@ def profiled_traffic(frames: int):
         return None
 
 
+def add_workload_rooflines(wl, mhz, sms=None):
+    """Fraction of the ALU roofline (f/g LLR updates per frame, counted by
+    the oracle, vs one update per FP32 lane per clock) and the batch latency
+    for every throughput workload; the adaptive one counts its L = 1 stage
+    only (a lower bound: escalated frames do more work)."""
+    path = os.path.join(ROOT, "tests", "golden", "work_per_frame.json")
+    if not mhz or not os.path.exists(path):
+        return
+    work = json.load(open(path))
+    if sms is None:
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * mhz * 1e6 / 1e9
+
+    def add(entry, key):
+        if not isinstance(entry, dict) or "ms" not in entry or key not in work:
+            return
+        ach = work[key]["fg_elems"] * entry["frames"] / (entry["ms"] / 1e3) / 1e9
+        entry["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s", "frac": ach / peak,
+                             "work": key}
+        entry.setdefault("latency_ms_batch", entry["ms"])
+
+    add(wl.get("c1_cascl_128_64_L4"), "c1_cascl_128_64_L4_L4_unpruned")
+    for k, e in (wl.get("c3_1024_512_L8") or {}).items():
+        add(e, "c3_1024_512_L8_L8_" + ("pruned" if k.endswith("_pruned") else "unpruned"))
+    for k, e in (wl.get("c2_fa_2048_1723") or {}).items():
+        add(e, "c2_2048_1723_L1_pruned")
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -630,6 +659,7 @@ def main():
             wl["c5_serving"] = run_c5()
         except Exception as e:
             wl["c5_serving"] = {"error": repr(e)}
+        add_workload_rooflines(wl, clocks.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median"))
         line["workloads"] = wl
         srv = wl.get("c5_serving", {})
         p99 = [v.get("p99_ms") for v in srv.values() if isinstance(v, dict) and v.get("p99_ms") is not None]
