@@ -315,8 +315,8 @@ static bool subtree_unpruned(const pscl_code_s *c, const pscl_pruning *pr, int o
     return subtree_unpruned(c, pr, o, S / 2) && subtree_unpruned(c, pr, o + S / 2, S / 2);
 }
 
-static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, int d, int o, int S, int side,
-                       std::vector<uint32_t> &ops, int &max_depth)
+static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, bool quad, int d, int o, int S,
+                       int side, std::vector<uint32_t> &ops, int &max_depth)
 {
     int type = classify(c, pr, o, S);
     if (type) {
@@ -341,6 +341,15 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, i
         if (d > max_depth) max_depth = d;
         return PSCL_OK;
     }
+    if (quad && d >= 1 && fuse == 4 && S == 16 && subtree_unpruned(c, pr, o, S)) {
+        // two levels of register-subtree pairs in one step (measured faster
+        // than separate steps for 4-leaf subtrees only)
+        uint32_t fz = 0;
+        for (int i = 0; i < S; i++) fz |= (uint32_t)c->frozen[o + i] << i;
+        ops.push_back(op_make(OP_RSUB4, (uint32_t)d, 0, (uint32_t)side, 0) | (fz << 16));
+        if (d > max_depth) max_depth = d;
+        return PSCL_OK;
+    }
     if (d >= 1 && fuse >= 2 && S == 2 * fuse && subtree_unpruned(c, pr, o, S)) {
         // f, both register subtrees, g and h in one step
         uint32_t fz = 0;
@@ -350,17 +359,17 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, i
         return PSCL_OK;
     }
     ops.push_back(op_make(OP_F, (uint32_t)d, 0, 0, 0));
-    int rc = gen_program(c, pr, fuse, d + 1, o, S / 2, 0, ops, max_depth);
+    int rc = gen_program(c, pr, fuse, quad, d + 1, o, S / 2, 0, ops, max_depth);
     if (rc) return rc;
     ops.push_back(op_make(OP_G, (uint32_t)d, 0, 0, 0));
-    rc = gen_program(c, pr, fuse, d + 1, o + S / 2, S / 2, 1, ops, max_depth);
+    rc = gen_program(c, pr, fuse, quad, d + 1, o + S / 2, S / 2, 1, ops, max_depth);
     if (rc) return rc;
     if (d > 0) ops.push_back(op_make(OP_COMB, (uint32_t)(d + 1), 0, (uint32_t)side, 0));
     return PSCL_OK;
 }
 
-// Peephole fusion of the schedule: a right register-subtree pair directly
-// followed by its parent's h step takes that step over.
+// Peephole fusion of the schedule: a right register-subtree pair (or quad)
+// directly followed by its parent's h step takes that step over.
 static void fuse_ops(std::vector<uint32_t> &ops)
 {
     std::vector<uint32_t> out;
@@ -369,7 +378,7 @@ static void fuse_ops(std::vector<uint32_t> &ops)
         const uint32_t a = ops[i];
         if (i + 1 < ops.size()) {
             const uint32_t b = ops[i + 1];
-            if (op_code(a) == OP_RSUB2 && op_side(a) == 1 && op_code(b) == OP_COMB &&
+            if ((op_code(a) == OP_RSUB2 || op_code(a) == OP_RSUB4) && op_side(a) == 1 && op_code(b) == OP_COMB &&
                 op_depth(b) == op_depth(a)) {
                 out.push_back(a | ((1u | ((uint32_t)op_side(b) << 1)) << 12));
                 i++;
@@ -381,10 +390,13 @@ static void fuse_ops(std::vector<uint32_t> &ops)
     ops.swap(out);
 }
 
-static std::vector<int> prune_key(const pscl_pruning *pr, int fuse)
+// Schedules depend on the pruning, the fusion size and whether the number
+// format is float (the 16-leaf quad step is used for float only: the
+// fixed-point kernels measured slower with it)
+static std::vector<int> prune_key(const pscl_pruning *pr, int fuse, bool fixed)
 {
-    if (!pr || pr->mask == 0) return {fuse, 0};
-    return {fuse, (int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
+    if (!pr || pr->mask == 0) return {fuse, fixed ? 1 : 0, 0};
+    return {fuse, fixed ? 1 : 0, (int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
 }
 
 static int check_pruning(const pscl_pruning *pr)
@@ -400,12 +412,12 @@ static int check_pruning(const pscl_pruning *pr)
     return PSCL_OK;
 }
 
-static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, Program *out)
+static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, bool fixed, Program *out)
 {
     int rc = check_pruning(pr);
     if (rc) return rc;
     const pscl_pruning *eff = (pr && pr->mask) ? pr : nullptr;
-    std::vector<int> key = prune_key(pr, fuse);
+    std::vector<int> key = prune_key(pr, fuse, fixed);
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->programs.find(key);
     if (it != c->programs.end()) {
@@ -414,7 +426,7 @@ static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, Program *o
     }
     std::vector<uint32_t> ops;
     int max_depth = 0;
-    rc = gen_program(c, eff, fuse, 0, 0, c->N, 1, ops, max_depth);
+    rc = gen_program(c, eff, fuse, !fixed, 0, 0, c->N, 1, ops, max_depth);
     if (rc) return rc;
     fuse_ops(ops);
     Program p;
@@ -435,11 +447,11 @@ static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, Program *o
 }
 
 // lookup of an already prepared schedule; never builds or allocates
-static int find_program(pscl_code c, const pscl_pruning *pr, int fuse, Program *out)
+static int find_program(pscl_code c, const pscl_pruning *pr, int fuse, bool fixed, Program *out)
 {
     int rc = check_pruning(pr);
     if (rc) return rc;
-    std::vector<int> key = prune_key(pr, fuse);
+    std::vector<int> key = prune_key(pr, fuse, fixed);
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->programs.find(key);
     if (it == c->programs.end())
@@ -457,11 +469,12 @@ extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
         std::lock_guard<std::mutex> lk(c->mu);
         for (auto &kv : c->tune) fuses.push_back(kv.second.second);
     }
-    for (int f : fuses) {
-        Program p;
-        int rc = get_program(c, pr, f, &p);
-        if (rc) return rc;
-    }
+    for (int f : fuses)
+        for (int fixed = 0; fixed < 2; ++fixed) {
+            Program p;
+            int rc = get_program(c, pr, f, fixed != 0, &p);
+            if (rc) return rc;
+        }
     return PSCL_OK;
 }
 
@@ -594,7 +607,8 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     if (dev != c->dev) return fail(PSCL_EINVAL, "code was created on device %d, current device is %d", c->dev, dev);
     int wps, fuse;
     tuning_for(c, L, (int)quant, pr, &wps, &fuse);
-    int rc = build_program ? get_program(c, pr, fuse, &pl->pg) : find_program(c, pr, fuse, &pl->pg);
+    const bool fixed = quant != PSCL_F32;
+    int rc = build_program ? get_program(c, pr, fuse, fixed, &pl->pg) : find_program(c, pr, fuse, fixed, &pl->pg);
     if (rc) return rc;
     DevProps dp;
     rc = get_props(&dp);
@@ -966,7 +980,7 @@ extern "C" int pscl_batch_create(const pscl_work_item *items, int n_items, pscl_
         }
         int wps_i, fuse_i;
         tuning_for(w.code, w.algo == PSCL_SC ? 1 : w.L, (int)w.quant, w.pruning, &wps_i, &fuse_i);
-        rc = get_program(w.code, w.pruning, fuse_i, &progs[(size_t)i]);
+        rc = get_program(w.code, w.pruning, fuse_i, w.quant != PSCL_F32, &progs[(size_t)i]);
         if (rc) { batch_free(b); return rc; }
     }
     void *p;
@@ -1233,7 +1247,7 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
         int wps, fuse;
         tuning_for(cx.code, cx.L, s->quant, cx.pruning, &wps, &fuse);
         Program pg;
-        rc = get_program(cx.code, cx.pruning, fuse, &pg);
+        rc = get_program(cx.code, cx.pruning, fuse, s->quant != PSCL_F32, &pg);
         if (rc) { server_free(s); return rc; }
         if (pg.has_nodes) s->nodes = true;
         Item &it = s->h_items[(size_t)i];

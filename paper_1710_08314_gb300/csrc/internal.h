@@ -27,6 +27,9 @@ enum Opcode : uint32_t {
                   //   children's LLRs never reach memory; bits 16..31 as above;
                   //   t = 1 | parent side << 1: the node is a right child and
                   //   the parent's h step (OP_COMB) is folded in
+    OP_RSUB4 = 6, // unpruned subtree of 16 leaves (H = 4) at depth d: four
+                  //   register subtrees of H leaves, the node's LLRs read once
+                  //   per quarter; fields as OP_RSUB2
 };
 enum NodeType : uint32_t { NT_R0 = 1, NT_R1 = 2, NT_REP = 3, NT_SPC = 4 };
 

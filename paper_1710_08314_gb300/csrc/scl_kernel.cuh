@@ -1007,6 +1007,47 @@ __device__ __forceinline__ void op_rsub(Ctx &c, int d, int side, uint32_t fz, ty
     if (side == 0) tab_set(c.idxS, d, c.slot);
 }
 
+// Partial sums (S <= 16 bits) of a node finished in registers: into BL_d or
+// BR_d, or, for a right child whose parent's h step is folded in (comb bit
+// 0; parent side in bit 1), combined with the left sibling's partial sums
+// (BL_d, the column the path holds) into BL/BR_{d-1}.
+template <int S>
+__device__ __forceinline__ void node_beta_out(Ctx &c, int d, int side, int comb, uint32_t beta)
+{
+    static_assert(S <= 16, "one 32-bit word for the parent");
+    if (comb & 1) {
+        constexpr uint32_t m2 = (1u << S) - 1u;
+        const int psd = comb >> 1;
+        const uint32_t sib = ld(c, bl_layer(c, d), c.seg + tab_get(c.idxS, d), c.P->lay.b_words[d], 8u);
+        uint32_t *dst = psd == 0 ? bl_layer(c, d - 1) : br_layer(c, d - 1);
+        st(c, dst, c.lane, c.P->lay.b_words[d - 1], ((sib ^ beta) & m2) | ((beta & m2) << S), 16u);
+        if (psd == 0) tab_set(c.idxS, d - 1, c.slot);
+        return;
+    }
+    uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
+    st(c, dst, c.lane, c.P->lay.b_words[d], beta, 64u);
+    if (side == 0) tab_set(c.idxS, d, c.slot);
+}
+
+// words of the node at depth d in the column the path holds (nw words)
+template <int NW>
+__device__ __forceinline__ void load_node(const Ctx &c, const uint32_t *in, int cin, uint32_t cap, uint32_t (&wd)[NW])
+{
+    if constexpr (NW >= 4) {
+#pragma unroll
+        for (int q = 0; q < NW / 4; ++q) {
+            const uint4 v = ld4(c, in, q, cin, 32, cap, 1u);
+            wd[4 * q] = v.x;
+            wd[4 * q + 1] = v.y;
+            wd[4 * q + 2] = v.z;
+            wd[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) wd[w] = ld(c, in, qa(w, cin, 32), cap, 1u);
+    }
+}
+
 // An unpruned node of 2H leaves at depth d: the f step, the left subtree in
 // registers, the g step (the node's LLRs read again from the column the path
 // holds after the left half's selections), the right subtree in registers and
@@ -1024,21 +1065,8 @@ __device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, int comb, uint
     auto carry = [&](int pl) { bl = __shfl_sync(PSCL_FULL, bl, pl); };
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
-        const int cin = c.seg + tab_get(c.idxL, d);
         uint32_t wd[NW];
-        if constexpr (NW >= 4) {
-#pragma unroll
-            for (int q = 0; q < NW / 4; ++q) {
-                const uint4 v = ld4(c, in, q, cin, 32, cap, 1u);
-                wd[4 * q] = v.x;
-                wd[4 * q + 1] = v.y;
-                wd[4 * q + 2] = v.z;
-                wd[4 * q + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int w = 0; w < NW; ++w) wd[w] = ld(c, in, qa(w, cin, 32), cap, 1u);
-        }
+        load_node<NW>(c, in, c.seg + tab_get(c.idxL, d), cap, wd);
         V a[H];
 #pragma unroll
         for (int i = 0; i < H; ++i) {
@@ -1051,21 +1079,58 @@ __device__ __forceinline__ void op_rsub2(Ctx &c, int d, int side, int comb, uint
         else br = beta;
     }
     constexpr uint32_t m = (1u << H) - 1u;
-    const uint32_t beta = ((bl ^ br) & m) | ((br & m) << H);
-    if (comb & 1) {
-        // right child: the parent's h step with the left sibling's partial
-        // sums (BL_d, the column the path holds), into BL/BR_{d-1}
-        constexpr uint32_t m2 = S >= 32 ? 0xFFFFFFFFu : ((1u << S) - 1u);
-        const int psd = comb >> 1;
-        const uint32_t sib = ld(c, bl_layer(c, d), c.seg + tab_get(c.idxS, d), c.P->lay.b_words[d], 8u);
-        uint32_t *dst = psd == 0 ? bl_layer(c, d - 1) : br_layer(c, d - 1);
-        st(c, dst, c.lane, c.P->lay.b_words[d - 1], ((sib ^ beta) & m2) | ((beta & m2) << S), 16u);
-        if (psd == 0) tab_set(c.idxS, d - 1, c.slot);
-        return;
+    node_beta_out<S>(c, d, side, comb, ((bl ^ br) & m) | ((br & m) << H));
+}
+
+// An unpruned node of 4H leaves (H = 4) at depth d, as four register
+// subtrees of H leaves: for each quarter the node's LLRs are read again (at
+// the column the path holds by then), the child's LLRs (f, or g with the
+// left child's partial sums) and the grandchild's (f, or g with its left
+// sibling's) are computed in registers, and the quarter is decoded.  The
+// partial sums kept so far follow the paths through the selections.  Neither
+// the children's nor the grandchildren's LLRs reach memory.  Equivalent to
+// F, RSUB2, G, RSUB2, COMB.
+template <class Qt, int H, bool OUT>
+__device__ __forceinline__ void op_rsub4(Ctx &c, int d, int side, int comb, uint32_t fz, typename Qt::V &pm)
+{
+    typedef typename Qt::V V;
+    constexpr int S = 4 * H, C = 2 * H;
+    constexpr int NW = (S + Qt::EPW - 1) / Qt::EPW;
+    constexpr uint32_t mh = (1u << H) - 1u, mc = (1u << C) - 1u;
+    const uint32_t *in = llr_layer(c, d);
+    const uint32_t cap = c.P->lay.llr_words[d];
+    // b0: first grandchild; b1: first child (after the second quarter);
+    // b2: third grandchild; b3: second child
+    uint32_t b0 = 0u, b1 = 0u, b2 = 0u, b3 = 0u;
+    auto carry = [&](int pl) {
+        b0 = __shfl_sync(PSCL_FULL, b0, pl);
+        b1 = __shfl_sync(PSCL_FULL, b1, pl);
+        b2 = __shfl_sync(PSCL_FULL, b2, pl);
+    };
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        uint32_t wd[NW];
+        load_node<NW>(c, in, c.seg + tab_get(c.idxL, d), cap, wd);
+        const bool right_child = q >= 2, right_gc = (q & 1) != 0;
+        const uint32_t sg = q < 2 ? b0 : b2;
+        V l[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const V x0 = Qt::elem(wd[i / Qt::EPW], i % Qt::EPW);
+            const V y0 = Qt::elem(wd[(i + C) / Qt::EPW], (i + C) % Qt::EPW);
+            const V x1 = Qt::elem(wd[(i + H) / Qt::EPW], (i + H) % Qt::EPW);
+            const V y1 = Qt::elem(wd[(i + H + C) / Qt::EPW], (i + H + C) % Qt::EPW);
+            const V a0 = right_child ? Qt::g1(x0, y0, (b1 >> i) & 1u) : Qt::f1(x0, y0);
+            const V a1 = right_child ? Qt::g1(x1, y1, (b1 >> (i + H)) & 1u) : Qt::f1(x1, y1);
+            l[i] = right_gc ? Qt::g1(a0, a1, (sg >> i) & 1u) : Qt::f1(a0, a1);
+        }
+        const uint32_t beta = rsub<Qt, H, OUT>(c, l, fz >> (q * H), pm, carry);
+        if (q == 0) b0 = beta;
+        else if (q == 1) b1 = ((b0 ^ beta) & mh) | ((beta & mh) << H);
+        else if (q == 2) b2 = beta;
+        else b3 = ((b2 ^ beta) & mh) | ((beta & mh) << H);
     }
-    uint32_t *dst = side == 0 ? bl_layer(c, d) : br_layer(c, d);
-    st(c, dst, c.lane, c.P->lay.b_words[d], beta, 64u);
-    if (side == 0) tab_set(c.idxS, d, c.slot);
+    node_beta_out<S>(c, d, side, comb, ((b1 ^ b3) & mc) | ((b3 & mc) << C));
 }
 
 // ---------------------------------------------------------------------------
@@ -1210,6 +1275,12 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
             case 8: op_rsub<Qt, 8, NODES>(c, d, op_side(op), fz, pm); break;
             default: op_rsub<Qt, 8, NODES>(c, d, op_side(op), fz, pm); break;  // host emits S <= 8
             }
+            break;
+        }
+        case OP_RSUB4: {
+            const uint32_t fz = op >> 16;
+            // the host emits 16-leaf quads for float schedules only
+            if constexpr (!Qt::FIXED) op_rsub4<Qt, 4, NODES>(c, d, op_side(op), op_t(op), fz, pm);
             break;
         }
         case OP_RSUB2: {
