@@ -1259,6 +1259,7 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
         make_layout(cx.code, pg, cx.L, s->quant, budget, &it.lay);
         it.L = cx.L;
         it.L_out = cx.L;
+        it.llr_cg = 1;
         it.stage_L = cx.L;
         if (it.lay.smem_per_warp > smem_pw) smem_pw = it.lay.smem_per_warp;
         if (it.lay.gmem_per_warp > gmem_pw) gmem_pw = it.lay.gmem_per_warp;

@@ -98,6 +98,8 @@ struct Item {
     int32_t *status_out;
     float *pm_out;
     uint32_t *err;              // debug error word (checked builds)
+    int llr_cg;                 // 1: read the channel LLRs past L1 (serving loop:
+                                //   a persistent kernel may see a reused buffer)
 };
 
 // bytes reserved at the head of each warp's shared slice for its Item copy,

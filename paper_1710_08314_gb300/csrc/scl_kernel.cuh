@@ -1246,7 +1246,10 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
                 float x = 0.0f;
                 if (i < c.N && f >= 0) {
                     const int col = __ldg(&cd.in_index[i]);
-                    if (col >= 0) x = __ldg(&P.llr[(size_t)f * (size_t)stride + col]);
+                    if (col >= 0) {
+                        const float *a = &P.llr[(size_t)f * (size_t)stride + col];
+                        x = P.llr_cg ? __ldcg(a) : __ldg(a);
+                    }
                 }
                 uint32_t q = Qt::quant(x);
                 word |= Qt::EPW == 1 ? q : (q << (e * Qt::BITS));

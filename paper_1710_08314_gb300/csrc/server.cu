@@ -178,7 +178,19 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
         }
         sleep_ns = 128;
         const int slot = k_found & (S.R - 1);
-        const SrvDReq d = S.dreq[slot];
+        // the slot is rewritten by whichever warp opens the ticket that reuses
+        // it: read it past this SM's L1, which may still hold the request the
+        // slot carried before
+        SrvDReq d;
+        {
+            const volatile SrvDReq *vd = S.dreq + slot;
+            d.ctx = vd->ctx;
+            d.n = vd->n;
+            d.llr = vd->llr;
+            d.info = vd->info;
+            d.status = vd->status;
+            d.t_open = vd->t_open;
+        }
         if (d.ctx != cur) {
             load_item(c, K.items + d.ctx, K, false);
             cur = d.ctx;

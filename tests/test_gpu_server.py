@@ -153,3 +153,37 @@ def test_burst_of_large_requests_all_complete():
     for r, (k, t, i, s) in enumerate(reqs):
         ri, rs = _reference(codes[k][1], t, codes[k][0]["L"])
         assert torch.equal(ri, i) and torch.equal(rs, s), f"request {r} differs from pscl_decode"
+
+
+def test_reused_request_buffers_are_read_afresh():
+    """A client that refills the same LLR buffer for its next request must
+    get the new frames decoded (the device loop outlives any cache)."""
+    import torch
+    from paper_1710_08314_gb300.polarscl import Server
+    codes, ctx = _contexts()
+    d, g = codes[1]
+    n = 64
+    contents = []
+    for r in range(6):
+        _, _, llr = make_inputs(d, n, d["ebn0_db"], 3000 + r)
+        contents.append(torch.from_numpy(llr).cuda())
+    llr_buf = torch.zeros_like(contents[0])
+    info = torch.zeros((n, g.nbytes), dtype=torch.uint8, device="cuda")
+    st = torch.zeros((n,), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    srv = Server(ctx, ring_slots=8, max_frames=64, idle_timeout_ms=20000)
+    got = []
+    try:
+        for r in range(6):
+            llr_buf.copy_(contents[r])
+            torch.cuda.current_stream().synchronize()
+            tk = srv.submit(1, llr_buf, info, st)
+            assert tk is not None
+            _wait(srv, [tk])
+            got.append((info.clone(), st.clone()))
+            torch.cuda.current_stream().synchronize()
+    finally:
+        srv.stop()
+    for r in range(6):
+        ri, rs = _reference(g, contents[r], d["L"])
+        assert torch.equal(ri, got[r][0]) and torch.equal(rs, got[r][1]), f"request {r}: stale input"
