@@ -583,12 +583,14 @@ struct Plan {
 static const int kWarpsPerBlock = 4;
 
 // shared-memory bytes per warp when wps warps (in blocks of four) share an
-// SM: what is left after the runtime's per-block reservation, evenly split
+// SM: each block gets an equal share of the SM's shared memory, less the
+// runtime's per-block reservation, rounded down to the 128-byte allocation
+// unit, split over its four warps
 static size_t slice_budget(const DevProps &dp, int wps)
 {
     const int blocks = (wps + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const long long usable = (long long)dp.smem_per_sm - (long long)blocks * dp.smem_reserved;
-    size_t budget = usable > 0 ? (size_t)usable / (size_t)(blocks * kWarpsPerBlock) : 0;
+    const long long per_block = (long long)dp.smem_per_sm / blocks - dp.smem_reserved;
+    size_t budget = per_block > 0 ? ((size_t)per_block & ~(size_t)127) / kWarpsPerBlock : 0;
     if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
     return budget & ~(size_t)15;
 }
