@@ -35,6 +35,13 @@
  *   - Fixed point (Sec. III-B-3): q = clamp(rint_half_even(lambda * 2^f), -Q, Q);
  *     every add saturates to [-Q, Q]; the PM shares the type and is
  *     normalised (minimum subtracted) after every node/leaf step.
+ *
+ * Pins (tests/test_oracle_*.py) tie every function to something outside
+ * itself (closed forms, catalogue values, brute-force ML, exact MAP metrics,
+ * an independent SC decoder).  Parity unpinned: the R1 and SPC handlers with a
+ * flip depth t smaller than the node size (Chase-t on large nodes) at L > 1;
+ * they are pinned only at L = 1 (classic SSC rules) and at t = node size
+ * (full enumeration, equal to the unpruned decoder).
  */
 #include <math.h>
 #include <stdint.h>
