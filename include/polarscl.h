@@ -101,10 +101,12 @@ int pscl_destroy_code(pscl_code code);
 /* Query code parameters (any pointer may be NULL).                          */
 int pscl_code_info(pscl_code code, int *N, int *K, int *K_info, int *n_punctured);
 
-/* Build (once per pruning setting) the node schedule the kernels walk for
- * this code, and cache it with the code.  pscl_decode calls this itself;
- * call it first when decodes will be captured in a CUDA graph, because the
- * first build makes a synchronous upload.                                   */
+/* Build (once per pruning setting) the node schedules the kernels walk for
+ * this code -- for the default and every tuned register-subtree size, in
+ * their float and fixed-point forms -- and cache them with the code.
+ * pscl_decode builds what it needs itself; call this first when decodes will
+ * be captured in a CUDA graph or use pscl_decode_static, because a build
+ * makes a synchronous upload.                                               */
 int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
 
 /* Record measured tuning for decodes of this code with list size L, number
