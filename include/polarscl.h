@@ -48,7 +48,7 @@ extern "C" {
 typedef struct pscl_code_s *pscl_code;
 
 /* Decoding algorithms (Sec. II-B): SC is the list of one; CASCL keeps L paths
- * and picks the best-metric candidate that passes the CRC (Sec. IV-A);
+ * and picks the best-metric candidate that passes the CRC (Sec. IV-B);
  * FASCL decodes with L = 1, 2, 4, ..., L and stops at the first CRC pass;
  * PASCL decodes with L = 1 and then directly with L.                        */
 typedef enum { PSCL_SC = 0, PSCL_CASCL = 1, PSCL_PASCL = 2, PSCL_FASCL = 3 } pscl_algo;
@@ -72,7 +72,7 @@ typedef enum { PSCL_F32 = 0, PSCL_I16 = 1, PSCL_I8 = 2 } pscl_quant;
  * rep_max: 0 = no limit (REP2+), 8 = REP8-.  spc_max: 4 = SPC4 (size 4
  * only), 0 = no limit (SPC4+).  r1_max: 0 = no limit.  r1_t / spc_t: how many
  * least-reliable positions the R1 / SPC candidates flip (r1_t = 2 is the
- * paper's Chase-2, Sec. IV-B); the kernels accept 1 <= r1_t <= 3 and
+ * paper's Chase-2, Sec. IV-C); the kernels accept 1 <= r1_t <= 3 and
  * 1 <= spc_t <= 4.  mask = 0 decodes the full tree leaf by leaf.            */
 typedef struct {
     uint32_t mask;

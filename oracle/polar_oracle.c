@@ -27,7 +27,7 @@
  *   - Candidates: path p (slot order) yields M candidates j; candidate id
  *     c = p*M + j; the min(L, n) smallest (PM, c) survive; survivors take new
  *     slots in increasing c.
- *   - Node handlers (Sec. II-B, IV-B): R0 one candidate; REP two (all-0,
+ *   - Node handlers (Sec. II-B, IV-C): R0 one candidate; REP two (all-0,
  *     all-1); R1 flips of the t least reliable positions (Chase-t, "two
  *     maximum" read as the two least reliable); SPC the even-parity subset of
  *     those flips.  Sums over node positions use a balanced pairwise tree over
@@ -38,10 +38,8 @@
  *
  * Pins (tests/test_oracle_*.py) tie every function to something outside
  * itself (closed forms, catalogue values, brute-force ML, exact MAP metrics,
- * an independent SC decoder).  Parity unpinned: the R1 and SPC handlers with a
- * flip depth t smaller than the node size (Chase-t on large nodes) at L > 1;
- * they are pinned only at L = 1 (classic SSC rules) and at t = node size
- * (full enumeration, equal to the unpruned decoder).
+ * an independent SC decoder, brute-force enumeration of the Chase-t and SPC
+ * candidate lists at flip depths below the node size with L > 1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -68,7 +66,7 @@ void orc_polar_transform(int N, uint8_t *v)
     orc_polar_transform(h, v + h);
 }
 
-/* CRC (Sec. II-A, Sec. IV-A): remainder of M(x) x^c divided by the generator
+/* CRC (Sec. II-A, Sec. IV-B): remainder of M(x) x^c divided by the generator
  * x^c + poly, bits taken MSB first (bits[0] is the highest power).          */
 uint32_t orc_crc(const uint8_t *bits, int nbits, int c, uint32_t poly)
 {
@@ -406,7 +404,7 @@ static int popcount_u(unsigned v)
 
 
 /* ------------------------------------------------------------------------ */
-/* Node handlers (Sec. II-B "Simplified SC and SCL", Sec. IV-B sorting).
+/* Node handlers (Sec. II-B "Simplified SC and SCL", Sec. IV-C sorting).
  * For one path at one node: M candidates, candidate j has a penalty and a
  * node codeword beta (the node's partial sums, S bits).                     */
 typedef struct {
@@ -624,7 +622,7 @@ static void scl_rec(dec_t *D, int Nv, int o_l, int o_s)
 }
 
 /* extract u_A from a decoded codeword x (systematic: x_A; otherwise the
- * transform is an involution, so u = x F) and check the CRC (Sec. IV-A).   */
+ * transform is an involution, so u = x F) and check the CRC (Sec. IV-B).   */
 static int extract_check(const orc_code *cd, const uint8_t *x, uint8_t *uA, uint8_t *work)
 {
     int N = cd->N;
@@ -648,7 +646,7 @@ typedef struct {
 } stage_result;
 
 /* One CA-SCL decode at list size L from the channel LLRs (Algorithm 1 and
- * select_best_path with sorted CRC checks, Sec. IV-A).                      */
+ * select_best_path with sorted CRC checks, Sec. IV-B).                      */
 static int scl_stage(const orc_code *cd, const double *llr_full, int L, const orc_pruning *pr,
                      const arith_t *A, orc_stats *st, uint8_t *info_out, double *pm_out,
                      uint8_t *paths_out, stage_result *res)

@@ -158,7 +158,7 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
         for (int k = 0; k < 8; k++) r = (r & 0x80000000u) ? ((r << 1) ^ p32) : (r << 1);
         lut[b] = r;
     }
-    // CRC check as a syndrome (Sec. IV-A): with the register starting at 0
+    // CRC check as a syndrome (Sec. IV-B): with the register starting at 0
     // the check "remainder of the first kinfo bits of u_A equals its last
     // crc_len bits" is linear over GF(2), so every position of A has a
     // crc_len-bit column and a path passes when the XOR of the columns of

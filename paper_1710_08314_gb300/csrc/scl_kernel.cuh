@@ -1187,7 +1187,7 @@ __device__ __forceinline__ uint32_t uword(const Ctx &c, int w, int col, int cl)
     return ld(c, ns, w * 32 + col, c.P->lay.ns_words, 512u);
 }
 
-// CRC check of the lane's path (Sec. IV-A): the first K_info bits of u_A feed
+// CRC check of the lane's path (Sec. IV-B): the first K_info bits of u_A feed
 // the CRC register (MSB first, starting at 0), the last c are compared with
 // the remainder.  The comparison is linear in the codeword, so it is computed
 // as a syndrome: one table lookup per codeword byte (XOR of the columns of the
@@ -1301,7 +1301,7 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         }
         __syncwarp();
     }
-    // final selection (Sec. IV-A): best metric among paths passing the CRC
+    // final selection (Sec. IV-B): best metric among paths passing the CRC
     const int cl = c.seg + tab_get(c.idxS, 1);
     if (!cd.systematic) {
         nonsys_transform(c, cl);

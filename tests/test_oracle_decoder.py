@@ -200,7 +200,7 @@ def test_quantiser_and_saturation_pins():
 
 
 def test_sorted_crc_check_equals_check_all_then_best():
-    """Sec. IV-A: checking candidates best-first and stopping at the first valid
+    """Sec. IV-B: checking candidates best-first and stopping at the first valid
     CRC is the same as checking all and taking the best valid one."""
     code, d = stored("c1_cascl_128_64_L4")
     A = np.flatnonzero(d["frozen"] == 0)
