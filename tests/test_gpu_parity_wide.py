@@ -1,0 +1,115 @@
+"""GPU decoder vs the oracle on many frames at the full size of the
+(2048, 1723 incl. CRC-32) L = 32 workload, in the launch configuration the
+benchmark times, and on the handler settings the smaller tests leave out
+(SPC nodes of any size, R1 flip depths 1 and 3, the allocation-free entry
+point).  Decoded bits, status and every slot's path metric must agree
+exactly (Algorithm 1, Sec. II-B; CRC selection Sec. IV-B)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import QMAP, AMAP, compare, describe, gpu_code, gpu_decode, make_inputs
+from oracle_pool import OraclePool
+
+pytestmark = pytest.mark.gpu
+
+HEADLINE = "c2_2048_1723"
+
+
+@pytest.fixture(scope="module")
+def pool():
+    with OraclePool() as p:
+        yield p
+
+
+def _bench_tuning(gcode, L, quant, llr_sample):
+    """The knobs the benchmark applies: the autotuner's cached (or measured)
+    choice for this code, list size and number format."""
+    import torch
+    from paper_1710_08314_gb300 import autotune
+    t = torch.from_numpy(np.ascontiguousarray(llr_sample, dtype=np.float32)).cuda()
+    tuning, _ = autotune.tuned(gcode, L, QMAP[quant][0], t)
+    return tuning
+
+
+@pytest.mark.parametrize("quant", ["f32", "i8"])
+@pytest.mark.parametrize("ebn0", [3.5, 4.5])
+def test_headline_launch_256_frames_over_every_warp_position(pool, quant, ebn0):
+    """16384 frames decoded in one launch as the benchmark does (one frame per
+    warp at L = 32, the tuned resident warps per SM, so frames land on every
+    SM, block slot and warp slot, and the second task round reuses each
+    warp's scratch); every 64th frame is checked against the oracle."""
+    d = synth.load_code(HEADLINE)
+    code, info, llr = make_inputs(d, 16384, ebn0, 500 + int(ebn0 * 10) + QMAP[quant][0])
+    gcode = gpu_code(d)
+    tuning = _bench_tuning(gcode, 32, quant, llr[:8192])
+    g = gpu_decode(gcode, llr, 32, "cascl", quant)
+    frames = np.arange(0, 16384, 64)
+    o = pool.decode(code, llr[frames], 32, oracle.CASCL, QMAP[quant][1])
+    bad = compare(g, o, frames)
+    assert not bad, f"tuning {tuning}: {len(bad)} mismatching frames; first: " + describe(g, o, bad[0], frames)
+    # far more frames than the oracle can take: at these SNRs the list
+    # decoder corrects nearly everything, and a scratch mix-up between warps
+    # would corrupt many frames
+    errs = int((g[0] != info).any(axis=1).sum())
+    assert errs <= (200 if ebn0 < 4 else 8), f"{errs} frame errors in 16384"
+
+
+SPC_ANY = dict(mask=15, rep_max=0, spc_max=0, r1_t=2, spc_t=4)        # SPC4+
+SPC_ANY_I8 = dict(mask=15, rep_max=8, spc_max=0, r1_t=2, spc_t=4)
+
+
+@pytest.mark.parametrize("quant", ["f32", "i16", "i8"])
+@pytest.mark.parametrize("name,L", [("c3_1024_512_L8", 8), ("mcs_512_256", 16), (HEADLINE, 32)])
+def test_spc_nodes_of_every_size(pool, quant, name, L):
+    from paper_1710_08314_gb300 import pruning
+    d = synth.load_code(name)
+    p = SPC_ANY_I8 if quant == "i8" else SPC_ANY
+    n = 128 if d["N"] == 2048 else 300
+    code, _, llr = make_inputs(d, n, 1.5 if d["N"] < 2048 else 3.5, 600 + L)
+    g = gpu_decode(gpu_code(d), llr, L, "cascl", quant, pruning(**p))
+    o = pool.decode(code, llr, L, oracle.CASCL, QMAP[quant][1], p)
+    bad = compare(g, o)
+    assert not bad, describe(g, o, bad[0])
+
+
+@pytest.mark.parametrize("r1_t", [1, 3])
+@pytest.mark.parametrize("quant", ["f32", "i8"])
+@pytest.mark.parametrize("name,L", [("c3_1024_512_L8", 8), ("mcs_256_128", 32), (HEADLINE, 32)])
+def test_r1_flip_depths_one_and_three(pool, r1_t, quant, name, L):
+    from paper_1710_08314_gb300 import pruning
+    d = synth.load_code(name)
+    p = dict(mask=15, rep_max=8 if quant == "i8" else 0, spc_max=4, r1_t=r1_t, spc_t=4)
+    n = 96 if d["N"] == 2048 else 250
+    code, _, llr = make_inputs(d, n, 1.5 if d["N"] < 2048 else 3.5, 700 + r1_t)
+    g = gpu_decode(gpu_code(d), llr, L, "cascl", quant, pruning(**p))
+    o = pool.decode(code, llr, L, oracle.CASCL, QMAP[quant][1], p)
+    bad = compare(g, o)
+    assert not bad, describe(g, o, bad[0])
+
+
+@pytest.mark.parametrize("algo,quant,prune", [("cascl", "f32", None), ("fascl", "i8", "i8"),
+                                              ("pascl", "f32", "all")])
+def test_static_entry_point_against_the_oracle(pool, algo, quant, prune):
+    """pscl_decode_static (fixed scratch inside the library) on 96 frames of
+    the full-size code, frame by frame against the oracle."""
+    import torch
+    from paper_1710_08314_gb300 import polarscl as ps, pruning
+    d = synth.load_code(HEADLINE)
+    p = None if prune is None else dict(mask=15, rep_max=8 if prune == "i8" else 0, spc_max=4, r1_t=2, spc_t=4)
+    gp = pruning(**p) if p else None
+    code, _, llr = make_inputs(d, 96, 3.5, 800 + AMAP[algo][0])
+    g = gpu_code(d)
+    ps.pscl_prepare(g.handle, gp)
+    t = torch.from_numpy(llr).cuda()
+    info = torch.empty((96, g.nbytes), dtype=torch.uint8, device="cuda")
+    st = torch.empty((96,), dtype=torch.int32, device="cuda")
+    pm = torch.empty((96, 32), dtype=torch.float32, device="cuda")
+    ps.pscl_decode_static(g.handle, t, 96, 32, AMAP[algo][0], gp, QMAP[quant][0], info, st, pm)
+    torch.cuda.synchronize()
+    from gpu_helpers import unpack_info
+    got = (unpack_info(info.cpu().numpy(), g.K_info), st.cpu().numpy(), pm.cpu().numpy())
+    o = pool.decode(code, llr, 32, AMAP[algo][1], QMAP[quant][1], p)
+    bad = compare(got, o)
+    assert not bad, describe(got, o, bad[0])
