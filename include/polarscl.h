@@ -130,9 +130,12 @@ int pscl_code_tune(pscl_code code, int L, pscl_quant quant, const pscl_pruning *
  * pm_out: device or NULL; n_frames x L float32 path metrics of the final
  *   stage in slot order (fixed point converted exactly), +inf for unused
  *   slots.
- * The library keeps a per-device scratch workspace that it grows on demand
- * (a synchronous cudaMalloc): call once outside stream capture before
- * capturing, or use pscl_decode_ws.                                          */
+ * The library keeps a scratch workspace per (device, stream) that it grows
+ * on demand (a cudaMalloc, after waiting for the stream's queued work when it
+ * replaces a smaller one): call once outside stream capture before capturing,
+ * or use pscl_decode_ws.  Calls on one stream share its workspace in stream
+ * order; calls on different streams use different workspaces and may run
+ * concurrently.                                                              */
 int pscl_decode(pscl_code code, const float *llr, int n_frames, int L, pscl_algo algo,
                 const pscl_pruning *pruning, pscl_quant quant, uint8_t *info_out,
                 int32_t *status_out, float *pm_out, void *stream);
@@ -160,6 +163,9 @@ int pscl_decode_ws(pscl_code code, const float *llr, int n_frames, int L, pscl_a
  * looks up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  The node schedule must already exist:
  * call pscl_prepare(code, pruning) at set-up (it allocates there).
+ * The schedule is looked up for the code's current tuning: after
+ * pscl_code_tune, pscl_set_fusion or pscl_set_tuning changes it, call
+ * pscl_prepare again (the autotuner does so for the codes it tunes).
  * Errors: PSCL_EINVAL when the schedule is not prepared or when one block's
  * per-warp scratch plus the adaptive frame lists (8 bytes per frame) exceed
  * 32 MiB; otherwise as pscl_decode.                                         */
@@ -217,33 +223,43 @@ int pscl_batch_info(pscl_batch batch, int *n_launches, int *n_tasks, size_t *scr
 
 /* ---------------------------------------------------------------------------
  * Serving loop: a device-resident request loop with continuous batching.
- * The server keeps its decoding contexts (code, list size, pruning; one
- * number format per server) and all frame state on the GPU and runs one
+ * The server keeps its decoding contexts (code, list size, pruning and
+ * number format per context) and all frame state on the GPU and runs one
  * persistent kernel on its own stream.  Requests are published through a
  * ring in mapped host memory; the kernel's warps take 32/L-frame tasks from
  * every open request, so requests that arrive while others decode share the
  * GPU with them at once.  Results equal pscl_decode's (CASCL, or SC for
- * L = 1) frame by frame.  Every device-side wait is bounded: after
- * idle_timeout_ms without any new request the kernel exits by itself and
- * pscl_server_status reports PSCL_ETIMEDOUT; pscl_server_stop raises an
- * abort word that the warps check between tasks.  While a server runs, wait
- * on streams or events only: a device-wide synchronisation waits for the
- * serving kernel itself, which ends only on stop or its idle budget.        */
+ * L = 1) frame by frame.  Admission (pscl_server_submit) needs a free ring
+ * slot, room in the frame budget and, with a byte budget, room in it for the
+ * request's device footprint (pscl_server_context_info); otherwise the
+ * request is deferred with PSCL_EAGAIN.  Every device-side wait is bounded:
+ * after idle_timeout_ms without any new request the kernel exits by itself,
+ * pscl_server_status reports PSCL_ETIMEDOUT and requests it never finished
+ * come back from pscl_server_poll with status PSCL_ETIMEDOUT;
+ * pscl_server_stop raises an abort word that the warps check between tasks.
+ * While a server runs, wait on streams or events only: a device-wide
+ * synchronisation (cudaDeviceSynchronize, and cudaFree, which implies one)
+ * waits for the serving kernel itself, which ends only on stop or its idle
+ * budget.  For the same reason the library defers its own frees on a device
+ * (pscl_destroy_code, pscl_batch_destroy, a replaced decode workspace) while
+ * a server runs there, and carries them out when the last one stops.      */
 typedef struct pscl_server_s *pscl_server;
 
 typedef struct {
     pscl_code code;
     int L;
     const pscl_pruning *pruning;  /* NULL = none (read at start only) */
+    pscl_quant quant;             /* number format of this context */
 } pscl_context;
 
 typedef struct {
     const pscl_context *contexts;
     int n_contexts;
-    pscl_quant quant;
     int ring_slots;               /* requests in flight at most, power of two */
     int max_frames_per_request;
     long long max_inflight_frames;/* admission budget (frames); 0 = ring x max */
+    long long hbm_budget_bytes;   /* admission budget (device bytes of the
+                                     frames in flight); 0 = none */
     int idle_timeout_ms;          /* device loop exits after this long idle */
     int max_warps;                /* 0 = every resident warp */
 } pscl_server_cfg;
@@ -271,11 +287,20 @@ typedef struct {
 
 /* Allocates the server's device and mapped memory and launches its kernel. */
 int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out);
-/* Thread-safe, non-blocking.  PSCL_EAGAIN when the ring or the frame budget
- * is full (nothing is dropped; retry), PSCL_EINVAL for a malformed request. */
+/* Thread-safe, non-blocking.  PSCL_EAGAIN when the ring, the frame budget or
+ * the byte budget is full (nothing is dropped; retry), PSCL_EINVAL for a
+ * malformed request or one larger than the whole byte budget.              */
 int pscl_server_submit(pscl_server s, const pscl_request *req, uint64_t *ticket);
 /* Collect up to max completed requests (non-blocking).                     */
 int pscl_server_poll(pscl_server s, pscl_completion *out, int max, int *n_out);
+/* Footprint of a context: the shared-memory slice and the global scratch
+ * slice its decode layout needs per warp (the server's warps hold the largest
+ * of each), and the device bytes one of its frames holds while in flight --
+ * its LLR row, its output row and status word, and its share (L/32) of a
+ * warp's scratch slice.  A request of n frames is charged n times that
+ * against hbm_budget_bytes until it completes.  Any pointer may be NULL.    */
+int pscl_server_context_info(pscl_server s, int context, size_t *smem_per_warp, size_t *scratch_per_warp,
+                             size_t *bytes_per_frame);
 /* running: kernel still resident; device_status: PSCL_ETIMEDOUT once it left
  * on its idle budget.                                                       */
 int pscl_server_status(pscl_server s, int *running, int *device_status, uint64_t *completed,
@@ -302,6 +327,16 @@ int pscl_set_fusion(int max_leaves);
  * skipped); *out = 0 when no workspace exists.  pscl_debug_checked: 1 in
  * the checked build, else 0.                                                */
 int pscl_debug_last_launches(void);
+/* pscl_debug_server_exit: for a serving loop that left on its idle budget,
+ * the warp that found the budget spent, how long it had been idle and the
+ * budget it compared with (ns), and tickets[4] = (opened, oldest open,
+ * being opened, published) at that moment.  Any pointer may be NULL.       */
+int pscl_debug_server_exit(pscl_server s, int *warp, long long *idle_ns, unsigned long long *budget_ns,
+                           uint32_t *tickets);
+/* pscl_debug_server_slots: after the serving kernel has ended, its per-slot
+ * device state (claim word, frames done, frame count; ring_slots entries
+ * each) and the ticket the host holds outstanding in each slot (~0 = free). */
+int pscl_debug_server_slots(pscl_server s, uint64_t *claim, uint32_t *done, int32_t *nframes, uint64_t *tickets);
 int pscl_debug_error_word(uint32_t *out);
 int pscl_debug_checked(void);
 

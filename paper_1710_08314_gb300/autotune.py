@@ -97,11 +97,13 @@ def tuned(code, L, quant, llr_sample=None, prune=None, algo=ps.PSCL_CASCL, path:
     hit = cache.get(key)
     if hit and not remeasure:
         ps.pscl_code_tune(code.handle, L, quant, hit["warps_per_sm"], hit["fuse"], prune)
+        ps.pscl_prepare(code.handle, prune)  # schedules for the tuned fusion size
         return (hit["warps_per_sm"], hit["fuse"]), False
     if llr_sample is None:
         return None, False
     results, best = measure(code, llr_sample, L, quant, prune, algo)
     ps.pscl_code_tune(code.handle, L, quant, best["warps_per_sm"], best["fuse"], prune)
+    ps.pscl_prepare(code.handle, prune)
     with _lock:
         cache = load_cache(path)
         cache[key] = dict(warps_per_sm=best["warps_per_sm"], fuse=best["fuse"], ms=best["ms"],

@@ -78,6 +78,54 @@ static int get_props(DevProps *out)
 }
 
 // ---------------------------------------------------------------------------
+// Releasing device memory.  cudaFree (and cudaFreeHost) wait for every kernel
+// on the device, and a serving loop's kernel runs until it is stopped or its
+// idle budget runs out: a free issued while a server runs on the device would
+// stall the caller for that long.  While any server runs on a device, the
+// library's own frees on that device are therefore queued and carried out
+// when the last server there stops.
+static std::mutex g_free_mu;
+static std::map<int, int> g_servers_running;                       // per device
+static std::map<int, std::vector<std::pair<void *, bool>>> g_deferred;  // (pointer, host)
+
+static void lib_free(void *p, bool host = false)
+{
+    if (!p) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_free_mu);
+        if (g_servers_running[dev] > 0) {
+            g_deferred[dev].push_back(std::make_pair(p, host));
+            return;
+        }
+    }
+    if (host) cudaFreeHost(p);
+    else cudaFree(p);
+}
+
+static void server_started(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_free_mu);
+    g_servers_running[dev]++;
+}
+
+// the server on `dev` has stopped: release what was queued once none is left
+static void server_stopped(int dev)
+{
+    std::vector<std::pair<void *, bool>> todo;
+    {
+        std::lock_guard<std::mutex> lk(g_free_mu);
+        if (--g_servers_running[dev] > 0) return;
+        todo.swap(g_deferred[dev]);
+    }
+    for (auto &pr : todo) {
+        if (pr.second) cudaFreeHost(pr.first);
+        else cudaFree(pr.first);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // code descriptor
 struct Program {
     uint32_t *d_ops = nullptr;
@@ -218,7 +266,7 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
     if (e == cudaSuccess) e = cudaMalloc(&c->d_blob, total);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_blob, blob.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        if (c->d_blob) cudaFree(c->d_blob);
+        lib_free(c->d_blob);
         delete c;
         return fail(e == cudaErrorMemoryAllocation ? PSCL_ENOMEM : PSCL_ECUDA, "create_code: %s",
                     cudaGetErrorString(e));
@@ -247,8 +295,8 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
 extern "C" int pscl_destroy_code(pscl_code c)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
-    for (auto &kv : c->programs) cudaFree(kv.second.d_ops);
-    cudaFree(c->d_blob);
+    for (auto &kv : c->programs) lib_free(kv.second.d_ops);
+    lib_free(c->d_blob);
     delete c;
     return PSCL_OK;
 }
@@ -438,7 +486,7 @@ static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, bool fixed
     CU(cudaMalloc(&p.d_ops, ops.size() * sizeof(uint32_t)));
     cudaError_t e = cudaMemcpy(p.d_ops, ops.data(), ops.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(p.d_ops);
+        lib_free(p.d_ops);
         return fail(PSCL_ECUDA, "program upload: %s", cudaGetErrorString(e));
     }
     c->programs[key] = p;
@@ -741,8 +789,10 @@ static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_a
     return PSCL_OK;
 }
 
-// library-owned workspace, one per device, grown on demand
-static std::map<int, std::pair<void *, size_t>> g_ws;
+// library-owned workspaces, one per (device, stream), grown on demand: calls
+// on one stream run in stream order and may share theirs, calls on different
+// streams never share one
+static std::map<std::pair<int, void *>, std::pair<void *, size_t>> g_ws;
 
 extern "C" int pscl_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_algo algo,
                            const pscl_pruning *pr, pscl_quant quant, uint8_t *info_out, int32_t *status_out,
@@ -757,11 +807,12 @@ extern "C" int pscl_decode(pscl_code c, const float *llr, int n_frames, int L, p
     size_t wsb;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        auto &slot = g_ws[dev];
+        auto &slot = g_ws[std::make_pair(dev, stream)];
         if (slot.second < pl.total_ws) {
             if (slot.first) {
-                CU(cudaDeviceSynchronize());
-                CU(cudaFree(slot.first));
+                // only this stream's queued work can still use the old one
+                CU(cudaStreamSynchronize((cudaStream_t)stream));
+                lib_free(slot.first);
                 slot.first = nullptr;
                 slot.second = 0;
             }
@@ -815,10 +866,13 @@ extern "C" int pscl_debug_error_word(uint32_t *out)
     int dev;
     CU(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_ws.find(dev);
     *out = 0;
-    if (it == g_ws.end() || !it->second.first) return PSCL_OK;
-    CU(cudaMemcpy(out, it->second.first, 4, cudaMemcpyDeviceToHost));
+    for (auto &kv : g_ws) {
+        if (kv.first.first != dev || !kv.second.first) continue;
+        uint32_t w = 0;
+        CU(cudaMemcpy(&w, kv.second.first, 4, cudaMemcpyDeviceToHost));
+        *out |= w;
+    }
     return PSCL_OK;
 }
 
@@ -946,7 +1000,7 @@ struct pscl_batch_s {
 
 static void batch_free(pscl_batch b)
 {
-    for (void *p : b->allocs) cudaFree(p);
+    for (void *p : b->allocs) lib_free(p);
     delete b;
 }
 
@@ -1176,13 +1230,22 @@ static uint64_t host_ns()
     return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
 }
 
+struct SrvCtxInfo {
+    size_t smem_per_warp = 0;     // shared-memory slice the context's layout needs
+    size_t scratch_per_warp = 0;  // global scratch slice the context's layout needs
+    size_t bytes_per_frame = 0;   // device bytes a frame of it holds while in flight
+};
+
 struct pscl_server_s {
     int dev = -1;
-    int quant = 0;
     bool nodes = false;
     int R = 0;
     int max_frames = 0;
     long long max_inflight = 0;
+    long long hbm_budget = 0;     // 0 = no byte budget
+    long long inflight_bytes = 0;
+    std::vector<SrvCtxInfo> ctx_info;
+    std::vector<long long> slot_bytes;
     int grid = 0, total_warps = 0;
     size_t smem_block = 0;
     std::vector<Item> h_items;
@@ -1206,11 +1269,11 @@ struct pscl_server_s {
 
 static void server_free(pscl_server s)
 {
-    if (s->d_items) cudaFree(s->d_items);
-    if (s->d_mem) cudaFree(s->d_mem);
-    if (s->ctl) cudaFreeHost(s->ctl);
-    if (s->ring) cudaFreeHost(s->ring);
-    if (s->comp) cudaFreeHost(s->comp);
+    lib_free(s->d_items);
+    lib_free(s->d_mem);
+    lib_free(s->ctl, true);
+    lib_free(s->ring, true);
+    lib_free(s->comp, true);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -1223,22 +1286,24 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
     if (R < 2 || R > 65536 || (R & (R - 1))) return fail(PSCL_EINVAL, "ring_slots=%d: a power of two in [2, 65536]", R);
     if (cfg->n_contexts < 1 || !cfg->contexts) return fail(PSCL_EINVAL, "no decoding contexts");
     if (cfg->max_frames_per_request < 1) return fail(PSCL_EINVAL, "max_frames_per_request < 1");
-    if (cfg->quant < PSCL_F32 || cfg->quant > PSCL_I8) return fail(PSCL_EINVAL, "unknown quantisation");
     if (cfg->idle_timeout_ms < 1) return fail(PSCL_EINVAL, "idle_timeout_ms < 1");
+    if (cfg->hbm_budget_bytes < 0) return fail(PSCL_EINVAL, "hbm_budget_bytes < 0");
     DevProps dp;
     int rc = get_props(&dp);
     if (rc) return rc;
     pscl_server s = new pscl_server_s();
     CU(cudaGetDevice(&s->dev));
-    s->quant = (int)cfg->quant;
     s->R = R;
     s->max_frames = cfg->max_frames_per_request;
     s->max_inflight = cfg->max_inflight_frames > 0 ? cfg->max_inflight_frames : (long long)R * cfg->max_frames_per_request;
+    s->hbm_budget = cfg->hbm_budget_bytes;
     // the serving kernel keeps 4 blocks of 4 warps per SM (its registers):
     // slices are sized for at most that many
     const size_t budget = slice_budget(dp, g_target_warps_per_sm < 16 ? g_target_warps_per_sm : 16);
     uint32_t smem_pw = 0, gmem_pw = 0;
+    unsigned quant_mask = 0;
     s->h_items.resize((size_t)cfg->n_contexts);
+    s->ctx_info.resize((size_t)cfg->n_contexts);
     for (int i = 0; i < cfg->n_contexts; i++) {
         const pscl_context &cx = cfg->contexts[i];
         if (!cx.code || cx.code->dev != s->dev) { server_free(s); return fail(PSCL_EINVAL, "context %d: bad code", i); }
@@ -1246,10 +1311,16 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
             server_free(s);
             return fail(PSCL_EINVAL, "context %d: L=%d", i, cx.L);
         }
+        if (cx.quant < PSCL_F32 || cx.quant > PSCL_I8) {
+            server_free(s);
+            return fail(PSCL_EINVAL, "context %d: unknown quantisation %d", i, (int)cx.quant);
+        }
+        const int q = (int)cx.quant;
+        quant_mask |= 1u << q;
         int wps, fuse;
-        tuning_for(cx.code, cx.L, s->quant, cx.pruning, &wps, &fuse);
+        tuning_for(cx.code, cx.L, q, cx.pruning, &wps, &fuse);
         Program pg;
-        rc = get_program(cx.code, cx.pruning, fuse, s->quant != PSCL_F32, &pg);
+        rc = get_program(cx.code, cx.pruning, fuse, q != PSCL_F32, &pg);
         if (rc) { server_free(s); return rc; }
         if (pg.has_nodes) s->nodes = true;
         Item &it = s->h_items[(size_t)i];
@@ -1258,18 +1329,31 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
         it.ops = pg.d_ops;
         it.n_ops = pg.n_ops;
         it.root_special = pg.root_special;
-        make_layout(cx.code, pg, cx.L, s->quant, budget, &it.lay);
+        make_layout(cx.code, pg, cx.L, q, budget, &it.lay);
         it.L = cx.L;
         it.L_out = cx.L;
         it.llr_cg = 1;
         it.stage_L = cx.L;
+        it.quant = q;
         if (it.lay.smem_per_warp > smem_pw) smem_pw = it.lay.smem_per_warp;
         if (it.lay.gmem_per_warp > gmem_pw) gmem_pw = it.lay.gmem_per_warp;
+        // device footprint of one frame in flight: its LLR row, its output
+        // row and status word, and its share of a warp's scratch slice
+        SrvCtxInfo &ci = s->ctx_info[(size_t)i];
+        ci.smem_per_warp = it.lay.smem_per_warp;
+        ci.scratch_per_warp = it.lay.gmem_per_warp;
+        ci.bytes_per_frame = (size_t)(cx.code->N - cx.code->P) * 4 + (size_t)((cx.code->kinfo + 7) / 8) + 4 +
+                             (size_t)it.lay.gmem_per_warp * (size_t)cx.L / 32;
+        if (s->hbm_budget > 0 && (long long)ci.bytes_per_frame > s->hbm_budget) {
+            server_free(s);
+            return fail(PSCL_EINVAL, "context %d: one frame needs %zu bytes, more than the HBM budget %lld", i,
+                        ci.bytes_per_frame, s->hbm_budget);
+        }
         s->codes.push_back(cx.code);
     }
     s->smem_block = (size_t)smem_pw * kWarpsPerBlock;
     int bps = 0;
-    cudaError_t e = server_attrs(s->quant, s->nodes, s->smem_block, &bps);
+    cudaError_t e = server_attrs(s->nodes, s->smem_block, &bps);
     if (e != cudaSuccess || bps < 1) {
         server_free(s);
         return fail(PSCL_EUNSUPPORTED, "server: no block fits (%zu bytes of shared memory)", s->smem_block);
@@ -1303,6 +1387,7 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
     s->slot_busy.assign((size_t)R, 0);
     s->slot_submit_ns.assign((size_t)R, 0);
     s->slot_frames.assign((size_t)R, 0);
+    s->slot_bytes.assign((size_t)R, 0);
     SrvParams P;
     memset(&P, 0, sizeof(P));
     P.K.items = s->d_items;
@@ -1311,6 +1396,7 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
     P.K.smem_per_warp = smem_pw;
     P.K.total_warps = s->total_warps;
     P.n_ctx = cfg->n_contexts;
+    P.quant_mask = quant_mask;
     void *dp_ctl, *dp_ring, *dp_comp;
     cudaHostGetDevicePointer(&dp_ctl, s->ctl, 0);
     cudaHostGetDevicePointer(&dp_ring, s->ring, 0);
@@ -1324,11 +1410,12 @@ extern "C" int pscl_server_start(const pscl_server_cfg *cfg, pscl_server *out)
     P.done = (uint32_t *)(s->d_mem + off_done);
     P.R = R;
     P.idle_ns = (unsigned long long)cfg->idle_timeout_ms * 1000000ull;
-    e = server_launch(s->quant, s->nodes, P, s->grid, s->smem_block, s->stream);
+    e = server_launch(s->nodes, P, s->grid, s->smem_block, s->stream);
     if (e != cudaSuccess) {
         server_free(s);
         return fail(PSCL_ECUDA, "server launch: %s", cudaGetErrorString(e));
     }
+    server_started(s->dev);
     s->running = true;
     *out = s;
     return PSCL_OK;
@@ -1343,11 +1430,17 @@ extern "C" int pscl_server_submit(pscl_server s, const pscl_request *req, uint64
         return fail(PSCL_EINVAL, "request of %d frames (1..%d)", req->n_frames, s->max_frames);
     if (!req->llr || !req->info_out || !req->status_out) return fail(PSCL_EINVAL, "request buffers are required");
     std::lock_guard<std::mutex> lk(s->mu);
+    if (s->running && *(volatile int32_t *)&s->ctl->exit_status != 0 && cudaStreamQuery(s->stream) == cudaSuccess)
+        s->running = false;  // the kernel left on its idle budget
     if (!s->running) return fail(PSCL_EINVAL, "server is stopped");
     const uint64_t t = s->next_ticket;
     const int slot = (int)(t & (uint64_t)(s->R - 1));
-    if (s->slot_busy[(size_t)slot] || s->inflight + req->n_frames > s->max_inflight)
-        return fail(PSCL_EAGAIN, "server full: %lld frames in flight", s->inflight);
+    const long long bytes = (long long)s->ctx_info[(size_t)req->context].bytes_per_frame * req->n_frames;
+    if (s->hbm_budget > 0 && bytes > s->hbm_budget)
+        return fail(PSCL_EINVAL, "request of %lld device bytes exceeds the whole HBM budget %lld", bytes, s->hbm_budget);
+    if (s->slot_busy[(size_t)slot] || s->inflight + req->n_frames > s->max_inflight ||
+        (s->hbm_budget > 0 && s->inflight_bytes + bytes > s->hbm_budget))
+        return fail(PSCL_EAGAIN, "server full: %lld frames (%lld bytes) in flight", s->inflight, s->inflight_bytes);
     SrvReq &r = s->ring[slot];
     r.ctx = req->context;
     r.n = req->n_frames;
@@ -1358,7 +1451,9 @@ extern "C" int pscl_server_submit(pscl_server s, const pscl_request *req, uint64
     s->slot_busy[(size_t)slot] = 1;
     s->slot_submit_ns[(size_t)slot] = host_ns();
     s->slot_frames[(size_t)slot] = req->n_frames;
+    s->slot_bytes[(size_t)slot] = bytes;
     s->inflight += req->n_frames;
+    s->inflight_bytes += bytes;
     s->next_ticket = t + 1;
     std::atomic_thread_fence(std::memory_order_seq_cst);
     *(volatile uint32_t *)&s->ctl->tail = (uint32_t)(t + 1);
@@ -1371,27 +1466,79 @@ extern "C" int pscl_server_poll(pscl_server s, pscl_completion *out, int max, in
 {
     if (!s || !n_out || (max > 0 && !out)) return fail(PSCL_EINVAL, "bad arguments");
     std::lock_guard<std::mutex> lk(s->mu);
+    // once the kernel has left (idle budget or stop), requests it never
+    // finished are reported as failed instead of staying outstanding
+    const int xs = *(volatile int32_t *)&s->ctl->exit_status;
+    const bool gone = xs != 0 && cudaStreamQuery(s->stream) == cudaSuccess;
+    if (gone) s->running = false;
     int n = 0;
     for (int slot = 0; slot < s->R && n < max; slot++) {
         if (!s->slot_busy[(size_t)slot]) continue;
         volatile SrvComp *c = s->comp + slot;
         const uint64_t t = s->slot_ticket[(size_t)slot];
-        if (c->seq != (uint32_t)(t + 1)) continue;
+        const bool done = c->seq == (uint32_t)(t + 1);
+        if (!done && !gone) continue;
         std::atomic_thread_fence(std::memory_order_acquire);
         pscl_completion &o = out[n++];
         o.ticket = t;
-        o.status = c->status;
+        o.status = done ? c->status : xs;
         o.n_frames = s->slot_frames[(size_t)slot];
         o.t_submit_ns = s->slot_submit_ns[(size_t)slot];
         o.t_done_ns = host_ns();
-        o.device_ns = c->t_end - c->t_open;
+        o.device_ns = done ? c->t_end - c->t_open : 0;
         s->slot_busy[(size_t)slot] = 0;
         s->inflight -= o.n_frames;
+        s->inflight_bytes -= s->slot_bytes[(size_t)slot];
         s->completed++;
     }
     *n_out = n;
-    if (s->running && s->ctl->exit_status == PSCL_ETIMEDOUT && cudaStreamQuery(s->stream) == cudaSuccess)
-        s->running = false;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_server_context_info(pscl_server s, int context, size_t *smem_per_warp, size_t *scratch_per_warp,
+                                        size_t *bytes_per_frame)
+{
+    if (!s) return fail(PSCL_EINVAL, "server is NULL");
+    if (context < 0 || context >= (int)s->ctx_info.size()) return fail(PSCL_EINVAL, "context %d out of range", context);
+    const SrvCtxInfo &ci = s->ctx_info[(size_t)context];
+    if (smem_per_warp) *smem_per_warp = ci.smem_per_warp;
+    if (scratch_per_warp) *scratch_per_warp = ci.scratch_per_warp;
+    if (bytes_per_frame) *bytes_per_frame = ci.bytes_per_frame;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_debug_server_exit(pscl_server s, int *warp, long long *idle_ns, unsigned long long *budget_ns,
+                                      uint32_t *tickets)
+{
+    if (!s) return fail(PSCL_EINVAL, "server is NULL");
+    volatile SrvCtl *c = s->ctl;
+    if (warp) *warp = (int)c->exit_warp;
+    if (idle_ns) *idle_ns = c->exit_idle_ns;
+    if (budget_ns) *budget_ns = c->exit_budget_ns;
+    if (tickets) {
+        tickets[0] = c->exit_opened;
+        tickets[1] = c->exit_head;
+        tickets[2] = c->exit_opening;
+        tickets[3] = c->exit_tail;
+    }
+    return PSCL_OK;
+}
+
+extern "C" int pscl_debug_server_slots(pscl_server s, uint64_t *claim, uint32_t *done, int32_t *nframes,
+                                       uint64_t *tickets)
+{
+    if (!s) return fail(PSCL_EINVAL, "server is NULL");
+    if (cudaStreamQuery(s->stream) != cudaSuccess) return fail(PSCL_EINVAL, "the serving kernel is still running");
+    const size_t R = (size_t)s->R;
+    const size_t off_dreq = 256, off_claim = off_dreq + sizeof(SrvDReq) * R, off_done = off_claim + 8 * R;
+    std::vector<SrvDReq> dr(R);
+    CU(cudaMemcpy(claim, s->d_mem + off_claim, 8 * R, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(done, s->d_mem + off_done, 4 * R, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(dr.data(), s->d_mem + off_dreq, sizeof(SrvDReq) * R, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < R; k++) {
+        nframes[k] = dr[k].n;
+        tickets[k] = s->slot_busy[k] ? s->slot_ticket[k] : ~0ull;
+    }
     return PSCL_OK;
 }
 
@@ -1428,6 +1575,8 @@ extern "C" int pscl_server_stop(pscl_server s, int timeout_ms)
         struct timespec ts = {0, 200000};
         nanosleep(&ts, nullptr);
     }
+    const int dev = s->dev;
     server_free(s);
+    server_stopped(dev);
     return PSCL_OK;
 }

@@ -100,6 +100,7 @@ struct Item {
     uint32_t *err;              // debug error word (checked builds)
     int llr_cg;                 // 1: read the channel LLRs past L1 (serving loop:
                                 //   a persistent kernel may see a reused buffer)
+    int quant;                  // number format (serving loop: chosen per context)
 };
 
 // bytes reserved at the head of each warp's shared slice for its Item copy,
@@ -155,7 +156,11 @@ struct SrvCtl {            // control block in mapped memory
     uint32_t tail;         // tickets published by the host
     uint32_t abort;        // host sets 1 to stop the loop
     int32_t exit_status;   // device: PSCL_ETIMEDOUT when it left on its idle budget
-    uint32_t pad;
+    uint32_t exit_warp;    // device: the warp that found the idle budget spent
+    long long exit_idle_ns;            // device: how long it had been idle
+    unsigned long long exit_budget_ns; // device: the budget it compared with
+    uint32_t exit_opened, exit_head;   // device: tickets opened / oldest open at that time
+    uint32_t exit_opening, exit_tail;
 };
 struct SrvDReq {           // device copy of an open request
     int ctx, n;
@@ -174,6 +179,7 @@ struct SrvDev {            // device-side counters
 struct SrvParams {
     KParams K;             // items, gmem, gmem_per_warp, smem_per_warp, total_warps
     int n_ctx;
+    unsigned quant_mask;   // number formats present among the contexts (bit q)
     SrvCtl *ctl;
     SrvReq *ring;
     SrvComp *comp;
@@ -185,8 +191,10 @@ struct SrvParams {
     unsigned long long idle_ns;
 };
 
-cudaError_t server_attrs(int quant, bool nodes, size_t smem, int *blocks_per_sm);
-cudaError_t server_launch(int quant, bool nodes, const SrvParams &S, int grid, size_t smem, cudaStream_t s);
+// one serving kernel decodes every number format (the item's quant field
+// selects the path at run time)
+cudaError_t server_attrs(bool nodes, size_t smem, int *blocks_per_sm);
+cudaError_t server_launch(bool nodes, const SrvParams &S, int grid, size_t smem, cudaStream_t s);
 
 struct EncParams {
     DevCode code;

@@ -11,9 +11,16 @@
 // memory.  Requests that arrive while others are decoding are admitted at
 // once and share the warps with them.
 //
+// Contexts may use different number formats: one kernel holds the float,
+// int16 and int8 decoders and each task takes the path of its context.
+//
 // Every wait is bounded: claims retry a bounded number of times, an idle warp
-// sleeps in short steps and leaves after idle_timeout without work (recording
-// PSCL_ETIMEDOUT), and the host's abort word stops all warps between tasks.
+// sleeps in short steps, and after idle_timeout without any new request the
+// first warp to notice records PSCL_ETIMEDOUT and raises the device abort word
+// so that every warp leaves together (no warp is left behind that could miss
+// a request nobody opens); the host's abort word stops all warps between
+// tasks.  Any warp that finds no work opens newly published requests before
+// it sleeps, so opening never depends on particular warps being alive.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -29,19 +36,49 @@
 
 namespace pscl {
 
+// device nanosecond timer, read as two 32-bit halves with the high half
+// checked on both sides of the low one (a read across a carry out of the low
+// half returns the later value)
 __device__ __forceinline__ unsigned long long gtimer()
 {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
+    uint32_t hi0, lo, hi1;
+    asm volatile("mov.u32 %0, %%globaltimer_hi;" : "=r"(hi0));
+    asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(lo));
+    asm volatile("mov.u32 %0, %%globaltimer_hi;" : "=r"(hi1));
+    if (hi1 != hi0) asm volatile("mov.u32 %0, %%globaltimer_lo;" : "=r"(lo));
+    return ((unsigned long long)hi1 << 32) | lo;
 }
 
-// copy newly published requests into device memory (one warp at a time)
+// Idle time of a warp, accumulated from the steps between its own timer
+// reads: a step counts at most kIdleStepNs and a timer that reads earlier
+// than before counts nothing, so the budget measures time this warp spent
+// looking for work, whatever the timer does between two reads.
+constexpr long long kIdleStepNs = 20000000;  // 20 ms: far above one loop step
+struct IdleClock {
+    unsigned long long prev;
+    long long idle;
+    __device__ void reset() { prev = gtimer(); idle = 0; }
+    __device__ long long tick()
+    {
+        const unsigned long long now = gtimer();
+        const long long d = (long long)(now - prev);
+        prev = now;
+        if (d > 0) idle += d < kIdleStepNs ? d : kIdleStepNs;
+        return idle;
+    }
+};
+
+// copy newly published requests into device memory (one warp at a time).
+// `opened` is read before the host's tail and the range is opened only when
+// the tail is ahead of it: a warp holding a tail value older than what
+// another warp has opened since must not open the range backwards (that
+// would walk 2^32 tickets and reset the claims of requests in flight).
 __device__ void srv_open(const SrvParams &S)
 {
-    const uint32_t t = *(volatile uint32_t *)&S.ctl->tail;
     const uint32_t op = *(volatile uint32_t *)&S.dev->opened;
-    if (t == op) return;
+    __threadfence();
+    const uint32_t t = *(volatile uint32_t *)&S.ctl->tail;
+    if ((int)(t - op) <= 0 || (int)(t - op) > S.R) return;
     if (atomicCAS(&S.dev->opening, op, t) != op) return;
     __threadfence_system();  // ring entries are read after the published count
     for (uint32_t k = op; k != t; ++k) {
@@ -80,7 +117,7 @@ __device__ int srv_try_claim(const SrvParams &S, uint32_t k, unsigned long long 
     return -1;
 }
 
-template <class Qt, bool NODES>
+template <bool NODES>
 __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ SrvParams S)
 {
     extern __shared__ __align__(16) char smem[];
@@ -93,7 +130,8 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
     c.gm = K.gmem + (size_t)gwarp * K.gmem_per_warp;
     c.P = (const Item *)c.sm;
     int cur = -1;
-    unsigned long long last_work = gtimer();
+    IdleClock idle;
+    idle.reset();
     uint32_t seen_opened = 0;
     unsigned sleep_ns = 128;
     const bool poller = (gwarp & 7) == 0;   // a few warps watch the host words
@@ -112,7 +150,7 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
             if (opened != seen_opened) {
                 // new requests anywhere keep every warp alive
                 seen_opened = opened;
-                last_work = gtimer();
+                idle.reset();
             }
         }
         stop = __shfl_sync(PSCL_FULL, stop, 0);
@@ -163,15 +201,36 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
             }
             if (k_found >= 0) break;
         }
-        if (c.lane == 0 && !stop && k_found < 0 && gtimer() - last_work > S.idle_ns) {
-            atomicCAS(&S.ctl->exit_status, 0, PSCL_ETIMEDOUT);
-            idle_out = 1;
+        if (c.lane == 0 && !stop && k_found < 0) {
+            // nothing to claim: open whatever the host has published since
+            // (any warp may; the CAS on `opening` lets one copy at a time)
+            srv_open(S);
+            if (*(volatile uint32_t *)&S.dev->opened != opened) {
+                idle.reset();
+            } else if (idle.tick() > (long long)S.idle_ns) {
+                // idle budget spent: every warp leaves (device abort word)
+                if (atomicCAS(&S.ctl->exit_status, 0, PSCL_ETIMEDOUT) == 0) {
+                    volatile SrvCtl *ctl = S.ctl;
+                    ctl->exit_warp = (uint32_t)gwarp;
+                    ctl->exit_idle_ns = idle.idle;
+                    ctl->exit_budget_ns = S.idle_ns;
+                    ctl->exit_opened = *(volatile uint32_t *)&S.dev->opened;
+                    ctl->exit_head = *(volatile uint32_t *)&S.dev->head;
+                    ctl->exit_opening = *(volatile uint32_t *)&S.dev->opening;
+                    ctl->exit_tail = ctl->tail;
+                    __threadfence_system();
+                }
+                atomicExch(&S.dev->abort, 1u);
+                idle_out = 1;
+            }
         }
         stop = __shfl_sync(PSCL_FULL, stop, 0);
         idle_out = __shfl_sync(PSCL_FULL, idle_out, 0);
         if (stop || idle_out) break;
         if (k_found < 0) {
-            // idle: bounded wait (the budget is checked above)
+            // idle: bounded wait (the budget is checked above); new requests
+            // opened just now are scanned without sleeping
+            if (__shfl_sync(PSCL_FULL, (int)(*(volatile uint32_t *)&S.dev->opened != opened), 0)) continue;
             __nanosleep(sleep_ns);
             sleep_ns = sleep_ns < 4096 ? sleep_ns * 2 : 4096;
             continue;
@@ -204,7 +263,11 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
             it->n_frames = d.n;
         }
         __syncwarp();
-        decode_task<Qt, NODES>(c, pos_found, d.n);
+        switch (c.P->quant) {
+        case 0: decode_task<QF32, NODES>(c, pos_found, d.n); break;
+        case 1: decode_task<QI16, NODES>(c, pos_found, d.n); break;
+        default: decode_task<QI8, NODES>(c, pos_found, d.n); break;
+        }
         if (c.lane == 0) {
             const int cnt = d.n - pos_found < c.fpw ? d.n - pos_found : c.fpw;
             __threadfence();
@@ -222,13 +285,13 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
             }
         }
         __syncwarp();
-        if (c.lane == 0) last_work = gtimer();
+        if (c.lane == 0) idle.reset();
     }
 }
 
 static std::mutex g_srv_attr_mu;
 
-template <class Qt, bool NODES>
+template <bool NODES>
 static cudaError_t srv_prepare(size_t smem, int *bps)
 {
     std::lock_guard<std::mutex> lk(g_srv_attr_mu);
@@ -236,30 +299,21 @@ static cudaError_t srv_prepare(size_t smem, int *bps)
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(server_kernel<Qt, NODES>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, server_kernel<Qt, NODES>, 128, smem);
+        e = cudaFuncSetAttribute(server_kernel<NODES>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, server_kernel<NODES>, 128, smem);
     return e;
 }
 
-template <class Qt, bool NODES>
-static cudaError_t srv_launch(const SrvParams &S, int grid, size_t smem, cudaStream_t s)
+cudaError_t server_attrs(bool nodes, size_t smem, int *bps)
 {
-    server_kernel<Qt, NODES><<<grid, 128, smem, s>>>(S);
+    return nodes ? srv_prepare<true>(smem, bps) : srv_prepare<false>(smem, bps);
+}
+
+cudaError_t server_launch(bool nodes, const SrvParams &S, int grid, size_t smem, cudaStream_t s)
+{
+    if (nodes) server_kernel<true><<<grid, 128, smem, s>>>(S);
+    else server_kernel<false><<<grid, 128, smem, s>>>(S);
     return cudaGetLastError();
-}
-
-cudaError_t server_attrs(int quant, bool nodes, size_t smem, int *bps)
-{
-    if (quant == 0) return nodes ? srv_prepare<QF32, true>(smem, bps) : srv_prepare<QF32, false>(smem, bps);
-    if (quant == 1) return nodes ? srv_prepare<QI16, true>(smem, bps) : srv_prepare<QI16, false>(smem, bps);
-    return nodes ? srv_prepare<QI8, true>(smem, bps) : srv_prepare<QI8, false>(smem, bps);
-}
-
-cudaError_t server_launch(int quant, bool nodes, const SrvParams &S, int grid, size_t smem, cudaStream_t s)
-{
-    if (quant == 0) return nodes ? srv_launch<QF32, true>(S, grid, smem, s) : srv_launch<QF32, false>(S, grid, smem, s);
-    if (quant == 1) return nodes ? srv_launch<QI16, true>(S, grid, smem, s) : srv_launch<QI16, false>(S, grid, smem, s);
-    return nodes ? srv_launch<QI8, true>(S, grid, smem, s) : srv_launch<QI8, false>(S, grid, smem, s);
 }
 
 }  // namespace pscl

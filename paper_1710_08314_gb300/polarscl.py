@@ -36,13 +36,13 @@ class pscl_work_item(C.Structure):
 
 
 class pscl_context(C.Structure):
-    _fields_ = [("code", C.c_void_p), ("L", C.c_int), ("pruning", C.c_void_p)]
+    _fields_ = [("code", C.c_void_p), ("L", C.c_int), ("pruning", C.c_void_p), ("quant", C.c_int)]
 
 
 class pscl_server_cfg(C.Structure):
-    _fields_ = [("contexts", C.c_void_p), ("n_contexts", C.c_int), ("quant", C.c_int), ("ring_slots", C.c_int),
+    _fields_ = [("contexts", C.c_void_p), ("n_contexts", C.c_int), ("ring_slots", C.c_int),
                 ("max_frames_per_request", C.c_int), ("max_inflight_frames", C.c_longlong),
-                ("idle_timeout_ms", C.c_int), ("max_warps", C.c_int)]
+                ("hbm_budget_bytes", C.c_longlong), ("idle_timeout_ms", C.c_int), ("max_warps", C.c_int)]
 
 
 class pscl_request(C.Structure):
@@ -94,6 +94,11 @@ def lib() -> C.CDLL:
             L.pscl_server_status.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_uint64),
                                              C.POINTER(C.c_longlong)]
             L.pscl_server_stop.argtypes = [vp, i]
+            L.pscl_debug_server_exit.argtypes = [vp, C.POINTER(i), C.POINTER(C.c_longlong),
+                                                 C.POINTER(C.c_ulonglong), vp]
+            L.pscl_debug_server_slots.argtypes = [vp, vp, vp, vp, vp]
+            L.pscl_server_context_info.argtypes = [vp, i, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                                   C.POINTER(C.c_size_t)]
             L.pscl_batch_create.argtypes = [vp, i, C.POINTER(vp)]
             L.pscl_batch_destroy.argtypes = [vp]
             L.pscl_batch_run.argtypes = [vp, vp, vp, vp, vp]
@@ -382,21 +387,48 @@ def pscl_server_stop(server, timeout_ms=5000):
     return _check(lib().pscl_server_stop(server, timeout_ms))
 
 
+def pscl_server_context_info(server, context):
+    a, b, c = C.c_size_t(), C.c_size_t(), C.c_size_t()
+    _check(lib().pscl_server_context_info(server, context, C.byref(a), C.byref(b), C.byref(c)))
+    return dict(smem_per_warp=a.value, scratch_per_warp=b.value, bytes_per_frame=c.value)
+
+
 class Server:
-    """Serving loop over a list of (Code, L, prune) contexts."""
+    """Serving loop over a list of (Code, L, prune[, quant]) contexts; a
+    context without its own number format takes `quant`."""
 
     def __init__(self, contexts, quant=PSCL_F32, ring_slots=256, max_frames=256, max_inflight=0,
-                 idle_timeout_ms=5000, max_warps=0):
+                 idle_timeout_ms=5000, max_warps=0, hbm_budget=0):
         self._ctx_arr = (pscl_context * len(contexts))()
         self._keep = []
-        for k, (code, L, prune) in enumerate(contexts):
+        for k, ctx in enumerate(contexts):
+            code, L, prune = ctx[:3]
             self._ctx_arr[k].code = code.handle.value
             self._ctx_arr[k].L = L
             self._ctx_arr[k].pruning = C.cast(C.pointer(prune), C.c_void_p) if prune is not None else None
+            self._ctx_arr[k].quant = ctx[3] if len(ctx) > 3 else quant
             self._keep.append((code, prune))
-        self.cfg = pscl_server_cfg(C.cast(self._ctx_arr, C.c_void_p).value, len(contexts), quant, ring_slots,
-                                   max_frames, max_inflight, idle_timeout_ms, max_warps)
+        self.cfg = pscl_server_cfg(C.cast(self._ctx_arr, C.c_void_p).value, len(contexts), ring_slots,
+                                   max_frames, max_inflight, hbm_budget, idle_timeout_ms, max_warps)
         self.handle = pscl_server_start(self.cfg)
+
+    def debug_exit(self):
+        w, i, b = C.c_int(), C.c_longlong(), C.c_ulonglong()
+        t = (C.c_uint32 * 4)()
+        _check(lib().pscl_debug_server_exit(self.handle, C.byref(w), C.byref(i), C.byref(b), C.cast(t, C.c_void_p)))
+        return dict(warp=w.value, idle_ns=i.value, budget_ns=b.value, opened=t[0], head=t[1], opening=t[2],
+                    tail=t[3])
+
+    def debug_slots(self):
+        R = self.cfg.ring_slots
+        cl, dn, nf, tk = (C.c_uint64 * R)(), (C.c_uint32 * R)(), (C.c_int32 * R)(), (C.c_uint64 * R)()
+        _check(lib().pscl_debug_server_slots(self.handle, C.cast(cl, C.c_void_p), C.cast(dn, C.c_void_p),
+                                             C.cast(nf, C.c_void_p), C.cast(tk, C.c_void_p)))
+        return [dict(slot=k, ticket=tk[k], claim_tag=cl[k] >> 32, claim_pos=cl[k] & 0xFFFFFFFF, done=dn[k], n=nf[k])
+                for k in range(R) if tk[k] != 2 ** 64 - 1]
+
+    def context_info(self, context):
+        return pscl_server_context_info(self.handle, context)
 
     def submit(self, context, llr, info_out, status_out):
         req = pscl_request(context, int(llr.shape[0]), llr.data_ptr(), info_out.data_ptr(), status_out.data_ptr())
