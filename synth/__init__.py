@@ -108,7 +108,21 @@ WORKLOADS = {
     "mcs_512_256": dict(N=512, K=256, crc_len=16, L=16, design_db=2.0, ebn0_db=2.0, P=0),
     "mcs_1024_512": dict(N=1024, K=512, crc_len=32, L=16, design_db=2.0, ebn0_db=2.0, P=0),
     "mcs_2048_1723": dict(N=2048, K=1723, crc_len=32, L=32, design_db=4.5, ebn0_db=4.0, P=0),
+    # list-size sweep (Sec. III-B-1, Fig. 3): (2048, 1024 incl. CRC-32), R = 1/2
+    "ls_2048_1024": dict(N=2048, K=1024, crc_len=32, L=32, design_db=2.0, ebn0_db=2.0, P=0),
 }
+
+# SPC4+ on/off study (Sec. III-B-2, Table 2): N in {256, 1024, 4096}, rate
+# K_info/N in {1/3, 1/2, 2/3}, list sizes 8 and 32; CRC-16 for N = 256 and
+# CRC-32 above (the table names no CRC); GA at 2 dB.
+for _n in (256, 1024, 4096):
+    for _num, _den in ((1, 3), (1, 2), (2, 3)):
+        _c = 16 if _n <= 256 else 32
+        WORKLOADS[f"spc_{_n}_r{_num}{_den}"] = dict(N=_n, K=round(_n * _num / _den) + _c, crc_len=_c, L=32,
+                                                   design_db=2.0, ebn0_db=2.0, P=0)
+# large codes (Sec. IV-D, Fig. 7: R = 1/2, L = 8)
+for _n in (4096, 8192):
+    WORKLOADS[f"ln_{_n}_{_n // 2}"] = dict(N=_n, K=_n // 2, crc_len=32, L=8, design_db=2.0, ebn0_db=2.0, P=0)
 
 
 def uneven_contexts(n_ctx: int = 48, seed: int = 7):

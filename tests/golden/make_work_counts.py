@@ -18,7 +18,9 @@ CASES = [
     ("c2_2048_1723", 32, None), ("c2_2048_1723", 32, "pruned"), ("c2_2048_1723", 1, None),
     ("c2_2048_1723", 1, "pruned"), ("c1_cascl_128_64_L4", 4, None), ("c3_1024_512_L8", 8, None),
     ("c3_1024_512_L8", 8, "pruned"),
-]
+] + [("ls_2048_1024", L, pk) for L in (1, 2, 4, 8, 16, 32) for pk in (None, "pruned")] + [
+    ("c2_2048_1723", L, "pruned") for L in (2, 4, 8, 16)] + [
+    (f"ln_{n}_{n // 2}", 8, None) for n in (4096, 8192)]
 
 
 def main():

@@ -1,6 +1,9 @@
-"""Host-side pieces of the benchmark: the per-workload roofline arithmetic."""
+"""Host-side pieces of the benchmark: the roofline arithmetic and the
+interpolation of the SNR at a target frame error rate."""
 import json
 import os
+
+import pytest
 
 import bench
 
@@ -8,20 +11,46 @@ import bench
 def test_workload_rooflines_use_the_oracle_work_counts():
     work = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "work_per_frame.json")))
     wl = {
-        "c1_cascl_128_64_L4": dict(value=1.0, frames=10000, ms=0.1),
-        "c3_1024_512_L8": {"f32_unpruned": dict(frames=100000, ms=10.0), "i16_pruned": dict(frames=100000, ms=20.0)},
-        "c2_fa_2048_1723": {"f32_4.5dB": dict(frames=200000, ms=10.0)},
+        "c1_cascl_128_64_L4": dict(value=1.0, frames=10000, ms=0.1, work="c1_cascl_128_64_L4_L4_unpruned",
+                                   quant="f32"),
+        "c3_1024_512_L8": {"i16_pruned_2.0dB": dict(frames=100000, ms=20.0, quant="i16",
+                                                    work="c3_1024_512_L8_L8_pruned")},
         "c4_uneven_500k": dict(frames=500000),
     }
     bench.add_workload_rooflines(wl, 2000.0, sms=152)
-    peak = 152 * 128 * 2000.0 * 1e6 / 1e9
     r = wl["c1_cascl_128_64_L4"]["roofline"]
-    assert r["peak"] == peak and r["bound"] == "alu"
-    assert abs(r["achieved"] - work["c1_cascl_128_64_L4_L4_unpruned"]["fg_elems"] * 10000 / 1e-4 / 1e9) < 1e-6
-    assert wl["c3_1024_512_L8"]["i16_pruned"]["roofline"]["work"] == "c3_1024_512_L8_L8_pruned"
-    assert wl["c3_1024_512_L8"]["f32_unpruned"]["roofline"]["work"] == "c3_1024_512_L8_L8_unpruned"
-    assert wl["c2_fa_2048_1723"]["f32_4.5dB"]["latency_ms_batch"] == 10.0
+    upd = work["c1_cascl_128_64_L4_L4_unpruned"]["fg_elems"] * 10000 / 1e-4
+    # shared-memory model: 12 bytes per float update against 128 B/clk/SM
+    assert r["bound"] == "smem" and r["peak"] == 128 * 152 * 2000.0 * 1e6 / 1e9
+    assert r["achieved"] == pytest.approx(upd * 12 / 1e9)
+    assert r["models"]["alu"]["peak"] == 152 * 128 * 2000.0 * 1e6 / 1e9
+    assert r["models"]["alu"]["achieved"] == pytest.approx(upd / 1e9)
+    r16 = wl["c3_1024_512_L8"]["i16_pruned_2.0dB"]["roofline"]
+    upd16 = work["c3_1024_512_L8_L8_pruned"]["fg_elems"] * 100000 / 0.02
+    assert r16["achieved"] == pytest.approx(upd16 * 6 / 1e9)
     assert "roofline" not in wl["c4_uneven_500k"]
-    wl2 = {"c1_cascl_128_64_L4": dict(frames=1, ms=1.0)}
+    wl2 = {"c1_cascl_128_64_L4": dict(frames=1, ms=1.0, work="c1_cascl_128_64_L4_L4_unpruned")}
     bench.add_workload_rooflines(wl2, None, sms=152)
     assert "roofline" not in wl2["c1_cascl_128_64_L4"]
+
+
+def test_issue_and_dram_models_need_a_profile():
+    m = bench.roofline_models(1000, 100, 1e-3, "i8", 2000.0, 152, hbm_gbs=6780.0)
+    assert set(m) == {"smem", "alu"}
+    assert m["smem"]["achieved"] == pytest.approx(1000 * 100 / 1e-3 * 3 / 1e9)
+    m = bench.roofline_models(1000, 100, 1e-3, "f32", 2000.0, 152, hbm_gbs=6780.0,
+                              prof={"dram_bytes_per_frame": 10 ** 6, "warp_instructions_per_frame": 4 * 10 ** 5})
+    assert m["dram"]["achieved"] == pytest.approx(100 * 1e6 / 1e-3 / 1e9)
+    assert m["dram"]["frac"] == pytest.approx(m["dram"]["achieved"] / 6780.0)
+    assert m["issue"]["peak"] == pytest.approx(152 * 4 * 2000.0 * 1e6 / 1e9)
+
+
+def test_snr_at_fer_interpolates_in_log_domain():
+    pts = [(1.0, 1e-2), (1.5, 1e-3), (2.0, 1e-5)]
+    assert bench.snr_at_fer(pts, 1e-3) == pytest.approx(1.5)
+    assert bench.snr_at_fer(pts, 1e-4) == pytest.approx(1.75)
+    assert bench.snr_at_fer(pts, 1e-7) is None
+
+
+def test_both_arms_report_the_same_config():
+    assert bench.headline_config("f32", bench.BATCH, 1) == bench.headline_config()
