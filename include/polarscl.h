@@ -8,7 +8,7 @@
  * partial sums in Sec. IV).
  *
  * Conventions shared by every call:
- *  - A code has length N = 2^n (8 <= N <= 2048), |A| = K information
+ *  - A code has length N = 2^n (8 <= N <= 8192), |A| = K information
  *    positions that INCLUDE the c CRC bits (K_info = K - c data bits).  Data
  *    bits then CRC bits fill A in increasing position order.  The CRC is the
  *    MSB-first remainder of the data bits times x^c modulo x^c + crc_poly
@@ -85,8 +85,12 @@ typedef struct {
 
 /* Create a code descriptor and upload it to the current CUDA device.
  * frozen: host, N bytes, nonzero = frozen; exactly N - K of them.
- * crc_len: 0, 8, 16 or 32; crc_poly: generator without its top bit
- * (e.g. 0x07, 0x1021, 0x04C11DB7); crc_len <= K.
+ * crc_len: 0..32 (any length: standard and custom CRCs, Sec. III-A);
+ * crc_poly: generator without its top bit, below 2^crc_len (e.g. 0x07,
+ * 0x1021, 0x04C11DB7, or 0x864CFB for a 24-bit CRC); crc_len <= K.
+ * N up to 8192: the decoder's slot tables cover schedule depths up to 12,
+ * which N = 8192 reaches only with register subtrees of 2 or more leaves
+ * (the default); a deeper schedule is refused with PSCL_EUNSUPPORTED.
  * puncture: host, N bytes, nonzero = not transmitted, or NULL.
  * systematic: 1 for systematic encoding (the paper's), 0 for x = u F.
  * On success *out owns device memory until pscl_destroy_code.

@@ -70,6 +70,11 @@ def lib():
             L.orc_ga_reliability.argtypes = [i, vp, d, vp]
             L.orc_ga_frozen.argtypes = [i, i, i, vp, d, vp, vp]
             L.orc_qup_pattern.argtypes = [i, i, vp]
+            L.orc_de_bms.argtypes = [i, vp, i, vp, vp, i, vp]
+            L.orc_de_awgn_channel.argtypes = [d, i, vp, vp]
+            L.orc_de_awgn_channel.restype = i
+            L.orc_de_reliability.argtypes = [i, vp, d, i, vp]
+            L.orc_de_frozen.argtypes = [i, i, i, vp, d, i, vp, vp]
             L.orc_decode.argtypes = [vp, vp, i, i, vp, i, i, d, vp, vp, vp, vp, vp]
             L.orc_decode_batch.argtypes = [vp, vp, i, i, i, vp, i, i, d, vp, vp, vp, vp]
             L.orc_sc_plain.argtypes = [vp, vp, vp, i, i, d, vp]
@@ -141,6 +146,39 @@ def ga_frozen(N, K, K_info, design_ebn0_db, punct=None):
     p = None if punct is None else np.ascontiguousarray(np.asarray(punct, dtype=np.uint8))
     lib().orc_ga_frozen(N, K, K_info, _ptr(p), float(design_ebn0_db), _ptr(fr), _ptr(z))
     return fr, z
+
+
+def de_bms(N, q, p, mu=64, punct=None):
+    """Density-evolution error-probability bounds of the N bit channels for a
+    channel given as a mixture of BSCs (weights q, crossovers p)."""
+    q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+    p = np.ascontiguousarray(np.asarray(p, dtype=np.float64))
+    pe = np.zeros(N, dtype=np.float64)
+    pu = None if punct is None else np.ascontiguousarray(np.asarray(punct, dtype=np.uint8))
+    lib().orc_de_bms(N, _ptr(pu), int(q.size), _ptr(q), _ptr(p), int(mu), _ptr(pe))
+    return pe
+
+
+def de_awgn_channel(sigma2, mu=64):
+    q = np.zeros(mu, dtype=np.float64)
+    p = np.zeros(mu, dtype=np.float64)
+    m = lib().orc_de_awgn_channel(float(sigma2), int(mu), _ptr(q), _ptr(p))
+    return q[:m], p[:m]
+
+
+def de_reliability(N, sigma2, mu=64, punct=None):
+    pe = np.zeros(N, dtype=np.float64)
+    pu = None if punct is None else np.ascontiguousarray(np.asarray(punct, dtype=np.uint8))
+    lib().orc_de_reliability(N, _ptr(pu), float(sigma2), int(mu), _ptr(pe))
+    return pe
+
+
+def de_frozen(N, K, K_info, design_ebn0_db, mu=64, punct=None):
+    fr = np.zeros(N, dtype=np.uint8)
+    pe = np.zeros(N, dtype=np.float64)
+    pu = None if punct is None else np.ascontiguousarray(np.asarray(punct, dtype=np.uint8))
+    lib().orc_de_frozen(N, K, K_info, _ptr(pu), float(design_ebn0_db), int(mu), _ptr(fr), _ptr(pe))
+    return fr, pe
 
 
 def qup_pattern(N, P):

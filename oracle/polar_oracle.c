@@ -220,6 +220,226 @@ void orc_ga_frozen(int N, int K, int K_info, const uint8_t *punct, double design
     free(z);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Density-evolution construction (Sec. II-A cites Tal and Vardy, "How to
+ * construct polar codes").  A binary memoryless symmetric channel is held as
+ * a mixture of binary symmetric channels: component j is used with
+ * probability q_j and flips the bit with probability p_j <= 1/2.  The two
+ * polarising transforms act on pairs of components:
+ *   check (left child):  p = p_a (1 - p_b) + p_b (1 - p_a),  weight q_a q_b;
+ *   variable (right child): the two observations agree with probability
+ *     s = p_a p_b + (1 - p_a)(1 - p_b), leaving a BSC of crossover
+ *     p_a p_b / s, or disagree, leaving min(p_a (1-p_b), p_b (1-p_a)) / (1-s).
+ * After each transform the mixture is brought back to at most mu components
+ * by merging all components whose capacity 1 - h2(p) falls in the same of mu
+ * equal bins: a merged component has the weighted mean crossover, which
+ * forgets which BSC was used, so the result is a degraded version of the true
+ * bit channel and its error probability sum_j q_j p_j is an upper bound.   */
+typedef struct {
+    double q, p;
+} de_comp;
+
+static double de_cap(double p)
+{
+    if (p <= 0.0) return 1.0;
+    if (p >= 0.5) return 0.0;
+    return 1.0 + p * log2(p) + (1.0 - p) * log2(1.0 - p);
+}
+
+/* merge m components into at most mu (binned by capacity); returns the count */
+static int de_merge(const de_comp *in, int m, int mu, de_comp *out, double *Q, double *E)
+{
+    for (int b = 0; b < mu; b++) Q[b] = E[b] = 0.0;
+    for (int j = 0; j < m; j++) {
+        if (in[j].q <= 0.0) continue;
+        int b = (int)(de_cap(in[j].p) * mu);
+        if (b >= mu) b = mu - 1;
+        if (b < 0) b = 0;
+        Q[b] += in[j].q;
+        E[b] += in[j].q * in[j].p;
+    }
+    int k = 0;
+    for (int b = 0; b < mu; b++)
+        if (Q[b] > 0.0) {
+            out[k].q = Q[b];
+            out[k].p = E[b] / Q[b];
+            k++;
+        }
+    return k;
+}
+
+typedef struct {
+    int mu;
+    de_comp *work;  /* 2 mu^2 components */
+    double *Q, *E;  /* mu bins */
+} de_ctx;
+
+static int de_check(const de_ctx *D, const de_comp *a, int na, const de_comp *b, int nb, de_comp *out)
+{
+    int m = 0;
+    for (int i = 0; i < na; i++)
+        for (int j = 0; j < nb; j++) {
+            D->work[m].q = a[i].q * b[j].q;
+            D->work[m].p = a[i].p * (1.0 - b[j].p) + b[j].p * (1.0 - a[i].p);
+            m++;
+        }
+    return de_merge(D->work, m, D->mu, out, D->Q, D->E);
+}
+
+static int de_var(const de_comp *D_a, int na, const de_comp *b, int nb, const de_ctx *D, de_comp *out)
+{
+    int m = 0;
+    for (int i = 0; i < na; i++)
+        for (int j = 0; j < nb; j++) {
+            double pa = D_a[i].p, pb = b[j].p, w = D_a[i].q * b[j].q;
+            double s = pa * pb + (1.0 - pa) * (1.0 - pb);
+            if (s > 0.0) {
+                D->work[m].q = w * s;
+                D->work[m].p = pa * pb / s;
+                m++;
+            }
+            if (s < 1.0) {
+                double x = pa * (1.0 - pb), y = pb * (1.0 - pa);
+                D->work[m].q = w * (1.0 - s);
+                D->work[m].p = (x < y ? x : y) / (1.0 - s);
+                m++;
+            }
+        }
+    return de_merge(D->work, m, D->mu, out, D->Q, D->E);
+}
+
+/* chans: S channels of at most mu components each (counts in cnt); writes
+ * the error-probability bound of each leaf channel in tree order */
+static void de_rec(const de_ctx *D, int S, const de_comp *chans, const int *cnt, double *pe, de_comp *tmp,
+                   int *tcnt)
+{
+    int mu = D->mu;
+    if (S == 1) {
+        double e = 0.0;
+        for (int j = 0; j < cnt[0]; j++) e += chans[j].q * chans[j].p;
+        pe[0] = e;
+        return;
+    }
+    int h = S / 2;
+    de_comp *child = tmp;
+    int *ccnt = tcnt;
+    for (int i = 0; i < h; i++)
+        ccnt[i] = de_check(D, chans + (size_t)i * mu, cnt[i], chans + (size_t)(i + h) * mu, cnt[i + h],
+                           child + (size_t)i * mu);
+    de_rec(D, h, child, ccnt, pe, tmp + (size_t)h * mu, tcnt + h);
+    for (int i = 0; i < h; i++)
+        ccnt[i] = de_var(chans + (size_t)i * mu, cnt[i], chans + (size_t)(i + h) * mu, cnt[i + h], D,
+                         child + (size_t)i * mu);
+    de_rec(D, h, child, ccnt, pe + h, tmp + (size_t)h * mu, tcnt + h);
+}
+
+/* Error-probability bounds of the N bit channels when every channel use is
+ * the BMS mixture (q[0..m), p[0..m)) and punctured positions carry nothing
+ * (a BSC with crossover 1/2).  m <= mu.                                      */
+void orc_de_bms(int N, const uint8_t *punct, int m, const double *q, const double *p, int mu, double *pe)
+{
+    de_ctx D;
+    D.mu = mu;
+    D.work = (de_comp *)malloc(sizeof(de_comp) * (size_t)(2 * mu * mu));
+    D.Q = (double *)malloc(sizeof(double) * (size_t)mu);
+    D.E = (double *)malloc(sizeof(double) * (size_t)mu);
+    de_comp *ch = (de_comp *)calloc((size_t)N * (size_t)mu, sizeof(de_comp));
+    de_comp *tmp = (de_comp *)calloc((size_t)(2 * N + 2) * (size_t)mu, sizeof(de_comp));
+    int *cnt = (int *)calloc((size_t)N, sizeof(int));
+    int *tcnt = (int *)calloc((size_t)(2 * N + 2), sizeof(int));
+    for (int i = 0; i < N; i++) {
+        if (punct && punct[i]) {
+            ch[(size_t)i * mu].q = 1.0;
+            ch[(size_t)i * mu].p = 0.5;
+            cnt[i] = 1;
+        } else {
+            for (int j = 0; j < m; j++) {
+                ch[(size_t)i * mu + j].q = q[j];
+                ch[(size_t)i * mu + j].p = p[j];
+            }
+            cnt[i] = m;
+        }
+    }
+    de_rec(&D, N, ch, cnt, pe, tmp, tcnt);
+    free(D.work); free(D.Q); free(D.E); free(ch); free(tmp); free(cnt); free(tcnt);
+}
+
+/* standard normal tail beyond x */
+static double q_tail(double x) { return 0.5 * erfc(x / sqrt(2.0)); }
+
+/* BPSK over AWGN of variance sigma2 as a mixture of mu BSCs: the reliability
+ * |LLR| = a of a channel output is a BSC with crossover 1 / (1 + e^a); the
+ * axis of a is cut where that BSC's capacity crosses b / mu, b = 1..mu-1, and
+ * the BSCs of each interval are merged (their mean crossover is the error
+ * mass of the interval over its probability).  With x = 0 sent, y ~ N(1,
+ * sigma2), LLR = 2 y / sigma2, |LLR| in [A, B) for y in +-[A, B) sigma2 / 2. */
+int orc_de_awgn_channel(double sigma2, int mu, double *q, double *p)
+{
+    double sigma = sqrt(sigma2);
+    double prev_a = 0.0;
+    int k = 0;
+    for (int b = 1; b <= mu; b++) {
+        double a;
+        if (b == mu) {
+            a = INFINITY;
+        } else {
+            /* capacity of the BSC at reliability a rises from 0 to 1: bisection */
+            double lo = 0.0, hi = 200.0, target = (double)b / mu;
+            for (int it = 0; it < 200; it++) {
+                double mid = 0.5 * (lo + hi);
+                if (de_cap(1.0 / (1.0 + exp(mid))) < target) lo = mid; else hi = mid;
+            }
+            a = 0.5 * (lo + hi);
+        }
+        double u = prev_a * sigma2 / 2.0, v = isinf(a) ? INFINITY : a * sigma2 / 2.0;
+        /* P(y in [u, v)) and P(y in (-v, -u]) for y ~ N(1, sigma2) */
+        double good = q_tail((u - 1.0) / sigma) - (isinf(v) ? 0.0 : q_tail((v - 1.0) / sigma));
+        double bad = q_tail((u + 1.0) / sigma) - (isinf(v) ? 0.0 : q_tail((v + 1.0) / sigma));
+        if (good + bad > 0.0) {
+            q[k] = good + bad;
+            p[k] = bad / (good + bad);
+            k++;
+        }
+        prev_a = a;
+    }
+    return k;
+}
+
+void orc_de_reliability(int N, const uint8_t *punct, double sigma2, int mu, double *pe)
+{
+    double *q = (double *)malloc(sizeof(double) * (size_t)mu);
+    double *p = (double *)malloc(sizeof(double) * (size_t)mu);
+    int m = orc_de_awgn_channel(sigma2, mu, q, p);
+    orc_de_bms(N, punct, m, q, p, mu, pe);
+    free(q);
+    free(p);
+}
+
+/* Frozen set from the bounds: the |A| = K channels with the smallest error
+ * probability carry information; ties go to the larger index.              */
+void orc_de_frozen(int N, int K, int K_info, const uint8_t *punct, double design_ebn0_db, int mu,
+                   uint8_t *frozen, double *pe_out)
+{
+    int P = 0;
+    if (punct)
+        for (int i = 0; i < N; i++) P += punct[i] ? 1 : 0;
+    double R = (double)K_info / (double)(N - P);
+    double sigma2 = 1.0 / (2.0 * R * pow(10.0, design_ebn0_db / 10.0));
+    double *pe = (double *)malloc(sizeof(double) * (size_t)N);
+    orc_de_reliability(N, punct, sigma2, mu, pe);
+    if (pe_out) memcpy(pe_out, pe, sizeof(double) * (size_t)N);
+    for (int i = 0; i < N; i++) frozen[i] = 1;
+    for (int k = 0; k < K; k++) {
+        int best = -1;
+        for (int i = 0; i < N; i++) {
+            if (!frozen[i]) continue;
+            if (best < 0 || pe[i] < pe[best] || (pe[i] == pe[best] && i > best)) best = i;
+        }
+        frozen[best] = 0;
+    }
+    free(pe);
+}
+
 /* Quasi-uniform puncturing (cited in Sec. III-A, Niu et al.): the first P
  * positions in bit-reversed order are not transmitted.                      */
 void orc_qup_pattern(int N, int P, uint8_t *punct)

@@ -55,6 +55,11 @@ void orc_ga_reliability(int N, const uint8_t *punct, double sigma2, double *z_le
 void orc_ga_frozen(int N, int K, int K_info, const uint8_t *punct, double design_ebn0_db,
                    uint8_t *frozen, double *z_out);
 void orc_qup_pattern(int N, int P, uint8_t *punct);
+void orc_de_bms(int N, const uint8_t *punct, int m, const double *q, const double *p, int mu, double *pe);
+int orc_de_awgn_channel(double sigma2, int mu, double *q, double *p);
+void orc_de_reliability(int N, const uint8_t *punct, double sigma2, int mu, double *pe);
+void orc_de_frozen(int N, int K, int K_info, const uint8_t *punct, double design_ebn0_db, int mu,
+                   uint8_t *frozen, double *pe_out);
 int orc_decode(const orc_code *cd, const double *llr, int L, int algo, const orc_pruning *pr,
                int mode, int wide_frac, double wide_q, uint8_t *info_out, int32_t *status,
                double *pm_out, uint8_t *paths_out, orc_stats *st);

@@ -160,10 +160,12 @@ extern "C" int pscl_create_code(int N, int K, const uint8_t *frozen, int crc_len
 {
     if (!out) return fail(PSCL_EINVAL, "out is NULL");
     *out = nullptr;
-    if (N < 8 || N > 2048 || (N & (N - 1))) return fail(PSCL_EINVAL, "N=%d: must be a power of two in [8, 2048]", N);
+    if (N < 8 || N > (1 << kMaxLog2N) || (N & (N - 1)))
+        return fail(PSCL_EINVAL, "N=%d: must be a power of two in [8, %d]", N, 1 << kMaxLog2N);
     if (!frozen) return fail(PSCL_EINVAL, "frozen is NULL");
-    if (crc_len != 0 && crc_len != 8 && crc_len != 16 && crc_len != 32)
-        return fail(PSCL_EINVAL, "crc_len=%d: must be 0, 8, 16 or 32", crc_len);
+    if (crc_len < 0 || crc_len > 32) return fail(PSCL_EINVAL, "crc_len=%d: must be 0..32", crc_len);
+    if (crc_len > 0 && crc_len < 32 && (crc_poly >> crc_len) != 0)
+        return fail(PSCL_EINVAL, "crc_poly 0x%x has bits above its %d-bit length", crc_poly, crc_len);
     int nf = 0;
     for (int i = 0; i < N; i++) nf += frozen[i] ? 1 : 0;
     if (N - nf != K || K < 1) return fail(PSCL_EINVAL, "K=%d but the frozen set leaves %d positions", K, N - nf);
@@ -476,6 +478,11 @@ static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, bool fixed
     int max_depth = 0;
     rc = gen_program(c, eff, fuse, !fixed, 0, 0, c->N, 1, ops, max_depth);
     if (rc) return rc;
+    if (max_depth > kTabLayers)
+        return fail(PSCL_EUNSUPPORTED,
+                    "N=%d with register subtrees of %d leaf(s): the schedule reaches depth %d, the kernels' slot "
+                    "tables hold %d layers (use subtrees of 2 or more leaves)",
+                    c->N, fuse, max_depth, kTabLayers);
     fuse_ops(ops);
     Program p;
     p.n_ops = (int)ops.size();
@@ -558,7 +565,8 @@ static void make_layout(const pscl_code_s *c, const Program &pg, int L, int quan
     // the warp's copy of its Item, then the selection scatter (64 words) and
     // frame ids (32 words)
     lay->src_off = kItemBytes + kPtabBytes;
-    so = align16(lay->src_off + 96 * 4);
+    lay->info_words = (uint32_t)std::max(64, (c->kinfo + 31) / 32);
+    so = align16(lay->src_off + (lay->info_words + 32) * 4);
     const int maxd = pg.max_depth;
     for (int d = maxd; d >= 0; d--) {
         const int S = c->N >> d;

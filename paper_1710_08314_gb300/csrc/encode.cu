@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const EncParams 
     if (frame >= P.n_frames) return;
     const DevCode &cd = P.code;
     const int N = cd.N, NW = N >= 32 ? N >> 5 : 1;
-    uint32_t *u = esm + warp * 64;
+    uint32_t *u = esm + warp * NW;  // the frame's N bits (NW words per warp)
     const int nbytes = (cd.kinfo + 7) >> 3;
     const uint8_t *info = P.info + (size_t)frame * (size_t)nbytes;
     // CRC of the data bits, MSB first (one lane; bytes through the table)
@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(32 * kEncWarps) encode_kernel(const EncParams 
 cudaError_t launch_encode(const EncParams &p, cudaStream_t s)
 {
     const int grid = (p.n_frames + kEncWarps - 1) / kEncWarps;
-    encode_kernel<<<grid, 32 * kEncWarps, kEncWarps * 64 * sizeof(uint32_t), s>>>(p);
+    const int NW = p.code.N >= 32 ? p.code.N >> 5 : 1;
+    encode_kernel<<<grid, 32 * kEncWarps, (size_t)kEncWarps * NW * sizeof(uint32_t), s>>>(p);
     return cudaGetLastError();
 }
 

@@ -6,8 +6,12 @@
 
 namespace pscl {
 
-constexpr int kMaxLog2N = 11;          // N <= 2048
+constexpr int kMaxLog2N = 13;          // N <= 8192
 constexpr int kMaxLayers = kMaxLog2N + 1;
+// per-path slot tables hold layers 1..kTabLayers (layer 0, the channel
+// LLRs, is shared by the paths of a frame): schedules deeper than that are
+// refused (with register subtrees of 2 or more leaves, N = 8192 fits)
+constexpr int kTabLayers = 12;
 
 // One instruction of the node schedule a warp walks for a code (the
 // pre-order traversal of Algorithm 1, with pruned nodes as single steps).
@@ -66,7 +70,9 @@ struct Layout {
     uint32_t br_off[kMaxLayers];
     uint32_t b_words[kMaxLayers];    // capacity of one beta buffer in words
     uint32_t llr_smem, bl_smem, br_smem;
-    uint32_t src_off;                // shared: selection scatter area (64 words)
+    uint32_t src_off;                // shared: selection scatter area (64 words) and the
+                                     //   info-bit buffer (info_words), then 32 frame ids
+    uint32_t info_words;             // max(64, ceil(K_info / 32))
     uint32_t ns_off;                 // global: non-systematic transform scratch
     uint32_t ns_words;
     uint32_t smem_per_warp;

@@ -153,20 +153,23 @@ struct Ctx {
     int n_active;    // warp-uniform
     const uint32_t *ops;
     int n_ops;
-    uint32_t idxL[2], idxS[2];  // per-layer slot tables, 6 x 5 bits per word
+    uint32_t idxL[2], idxS[2];  // per-layer slot tables: layers 1..12, 6 x 5 bits per word
 };
 
+// slot of layer d (1 <= d <= kTabLayers) in a table
 __device__ __forceinline__ int tab_get(const uint32_t (&t)[2], int d)
 {
-    uint32_t w = d < 6 ? t[0] : t[1];
-    int sh = 5 * (d < 6 ? d : d - 6);
+    const int e = d - 1;
+    uint32_t w = e < 6 ? t[0] : t[1];
+    int sh = 5 * (e < 6 ? e : e - 6);
     return (int)((w >> sh) & 31u);
 }
 __device__ __forceinline__ void tab_set(uint32_t (&t)[2], int d, int v)
 {
-    int sh = 5 * (d < 6 ? d : d - 6);
+    const int e = d - 1;
+    int sh = 5 * (e < 6 ? e : e - 6);
     uint32_t m = ~(31u << sh);
-    if (d < 6) t[0] = (t[0] & m) | ((uint32_t)v << sh);
+    if (e < 6) t[0] = (t[0] & m) | ((uint32_t)v << sh);
     else t[1] = (t[1] & m) | ((uint32_t)v << sh);
 }
 __device__ __forceinline__ void tab_fill(uint32_t (&t)[2], int v)
@@ -1221,7 +1224,7 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     typedef typename Qt::V V;
     const Item &P = *c.P;
     const DevCode &cd = P.code;
-    int32_t *fids = (int32_t *)(c.sm + P.lay.src_off) + 64;  // 32 frame ids
+    int32_t *fids = (int32_t *)(c.sm + P.lay.src_off) + P.lay.info_words;  // 32 frame ids
     // frame id of this lane's frame (-1: none)
     const int pos = pos0 + c.fiw;
     {
@@ -1320,7 +1323,7 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     const int wcol = c.seg + win;
     const int wcl = __shfl_sync(PSCL_FULL, cl, wcol);
     // frame ids from shared memory (not kept in registers across the walk)
-    const int32_t *fid = (const int32_t *)(c.sm + P.lay.src_off) + 64;
+    const int32_t *fid = (const int32_t *)(c.sm + P.lay.src_off) + P.lay.info_words;
     const int frame = fid[c.fiw];
     if (frame >= 0) {
         if (c.slot == 0) {
@@ -1344,15 +1347,14 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     // out MSB first.
     const int nbytes = (cd.kinfo + 7) >> 3;
     const int NB = c.N >> 3;
-    uint32_t *buf = (uint32_t *)(c.sm + P.lay.src_off);  // 64 words: K_info <= 2048
+    uint32_t *buf = (uint32_t *)(c.sm + P.lay.src_off);  // info_words words: K_info bits
     for (int f = 0; f < c.fpw; ++f) {
         const int fr = fid[f];
         const int wc = __shfl_sync(PSCL_FULL, wcol, f * c.L);
         const int wl = __shfl_sync(PSCL_FULL, wcl, f * c.L);
         if (fr < 0) continue;  // warp-uniform
         __syncwarp();
-        buf[c.lane] = 0u;
-        buf[c.lane + 32] = 0u;
+        for (int w = c.lane; w < (int)P.lay.info_words; w += 32) buf[w] = 0u;
         __syncwarp();
         for (int q0 = 4 * c.lane; q0 < NB; q0 += 128) {
             const uint32_t x = uword(c, q0 >> 2, wc, wl);

@@ -94,6 +94,9 @@ def torch_bpsk_awgn_llr(x_bits, sigma, generator, punct_keep_idx=None):
 # Frozen sets are stored files written by tests/golden/make_codes.py.
 
 CRC_POLYS = {0: 0, 8: 0x07, 16: 0x1021, 32: 0x04C11DB7}
+# further generators, without their top bit: the 6-, 11- and 24-bit CRCs of
+# the 5G NR channel coding (D^6+D^5+1, D^11+D^10+D^9+D^5+1, CRC24C)
+CUSTOM_CRC_POLYS = {6: 0x21, 11: 0x621, 24: 0xB2B117}
 
 WORKLOADS = {
     # plain CA-SCL, (128, 64 incl. CRC-8), L=4, fp32, unpruned, GA at 2.0 dB
@@ -120,6 +123,13 @@ for _n in (256, 1024, 4096):
         _c = 16 if _n <= 256 else 32
         WORKLOADS[f"spc_{_n}_r{_num}{_den}"] = dict(N=_n, K=round(_n * _num / _den) + _c, crc_len=_c, L=32,
                                                    design_db=2.0, ebn0_db=2.0, P=0)
+# custom CRC lengths (Sec. III-A: any CRC can be defined)
+for _c in (6, 11, 24):
+    WORKLOADS[f"crc{_c}_512_256"] = dict(N=512, K=256, crc_len=_c, L=8, design_db=2.0, ebn0_db=2.0, P=0,
+                                        crc_poly=CUSTOM_CRC_POLYS[_c])
+# a density-evolution frozen set (Sec. II-A, Tal-Vardy) for the (1024, 512) code
+WORKLOADS["de_1024_512"] = dict(N=1024, K=512, crc_len=16, L=8, design_db=2.0, ebn0_db=2.0, P=0,
+                                construction="de")
 # large codes (Sec. IV-D, Fig. 7: R = 1/2, L = 8)
 for _n in (4096, 8192):
     WORKLOADS[f"ln_{_n}_{_n // 2}"] = dict(N=_n, K=_n // 2, crc_len=32, L=8, design_db=2.0, ebn0_db=2.0, P=0)

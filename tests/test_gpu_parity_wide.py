@@ -113,3 +113,69 @@ def test_static_entry_point_against_the_oracle(pool, algo, quant, prune):
     o = pool.decode(code, llr, 32, AMAP[algo][1], QMAP[quant][1], p)
     bad = compare(got, o)
     assert not bad, describe(got, o, bad[0])
+
+
+@pytest.mark.parametrize("name", ["ln_4096_2048", "ln_8192_4096"])
+@pytest.mark.parametrize("quant,prune", [("f32", None), ("f32", "all"), ("i8", "i8"), ("i16", None)])
+def test_large_codes(pool, name, quant, prune):
+    """N = 4096 and 8192 (R = 1/2, CRC-32, L = 8; Sec. IV-D studies codes
+    this long): the upper LLR layers live in global scratch and the slot
+    tables reach depth 12."""
+    from paper_1710_08314_gb300 import pruning
+    d = synth.load_code(name)
+    p = None if prune is None else dict(mask=15, rep_max=8 if prune == "i8" else 0, spc_max=4, r1_t=2, spc_t=4)
+    n = 64 if d["N"] == 4096 else 32
+    code, _, llr = make_inputs(d, n, 1.5, 900 + d["N"] // 1024)
+    g = gpu_decode(gpu_code(d), llr, 8, "cascl", quant, pruning(**p) if p else None)
+    o = pool.decode(code, llr, 8, oracle.CASCL, QMAP[quant][1], p)
+    bad = compare(g, o)
+    assert not bad, describe(g, o, bad[0])
+
+
+def test_large_code_adaptive_and_full_list():
+    """N = 4096 with FA up to L = 32 and a plain L = 32 decode (sampled)."""
+    d = synth.load_code("ln_4096_2048")
+    code, _, llr = make_inputs(d, 40, 1.25, 950)
+    gcode = gpu_code(d)
+    for algo, L, quant in [("fascl", 32, "f32"), ("cascl", 32, "i8")]:
+        g = gpu_decode(gcode, llr, L, algo, quant)
+        frames = np.array([0, 13, 39])
+        from gpu_helpers import oracle_decode
+        o = oracle_decode(code, llr[frames], L, algo, quant)
+        bad = compare(g, o, frames)
+        assert not bad, describe(g, o, bad[0], frames)
+
+
+def test_depth_beyond_the_slot_tables_is_refused():
+    """N = 8192 without register subtrees would reach depth 13: refused."""
+    import torch
+    from paper_1710_08314_gb300 import polarscl as ps
+    d = synth.load_code("ln_8192_4096")
+    g = gpu_code(d)
+    ps.pscl_set_fusion(1)
+    try:
+        with pytest.raises(ps.PsclError) as e:
+            g.decode(torch.zeros((4, 8192), device="cuda"), 8)
+        assert e.value.code == ps.PSCL_EUNSUPPORTED
+    finally:
+        ps.pscl_set_fusion(8)
+
+
+@pytest.mark.parametrize("name", ["crc6_512_256", "crc11_512_256", "crc24_512_256", "de_1024_512"])
+def test_custom_crcs_and_density_evolution_codes(pool, name):
+    """CRCs of 6, 11 and 24 bits (Sec. III-A: custom CRCs) and a frozen set
+    from density evolution (Sec. II-A): encoder and decoder against the
+    oracle."""
+    import torch
+    from paper_1710_08314_gb300 import pruning
+    d = synth.load_code(name)
+    code, info, llr = make_inputs(d, 200, 1.5, 970)
+    g = gpu_code(d)
+    x = oracle.encode(code, info)
+    xg = g.encode(torch.from_numpy(np.packbits(info, axis=1)).cuda()).cpu().numpy()
+    assert np.array_equal(xg, x)
+    for quant, p in [("f32", None), ("i8", dict(mask=15, rep_max=8, spc_max=4, r1_t=2, spc_t=4))]:
+        got = gpu_decode(g, llr, 8, "cascl", quant, pruning(**p) if p else None)
+        ref = pool.decode(code, llr, 8, oracle.CASCL, QMAP[quant][1], p)
+        bad = compare(got, ref)
+        assert not bad, describe(got, ref, bad[0])
