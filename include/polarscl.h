@@ -323,6 +323,14 @@ int pscl_server_stop(pscl_server s, int timeout_ms);
  *   depend on either.  PSCL_EINVAL outside the ranges.                      */
 int pscl_set_tuning(int target_warps_per_sm);
 int pscl_set_fusion(int max_leaves);
+/* pscl_set_sc_kernel: 1 (default) decodes one-path stages (PSCL_SC, and the
+ * first stage of PSCL_FASCL and PSCL_PASCL) of batches up to four waves of
+ * resident warps with a warp per frame and all of a frame's LLR layers and
+ * partial sums in shared memory (lowest latency); larger batches, and every
+ * batch with 0, go to the list kernel, which decodes 32 such frames per warp
+ * (highest throughput).  Results are identical; not thread-safe against
+ * concurrent decodes.                                                       */
+int pscl_set_sc_kernel(int enable);
 
 /* Test hooks.  pscl_debug_last_launches: kernel launches of the calling
  * process's most recent decode or batch run.  pscl_debug_error_word: the

@@ -418,6 +418,35 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, b
     return PSCL_OK;
 }
 
+// The schedule of the one-path (SC) kernel: the same pruned tree without
+// register subtrees; every step carries its node's leaf offset in bits
+// 16..31 (an h step the offset of the node it completes).
+// Unpruned subtrees of up to kScFuse leaves are one step (OP_RSUB, decoded
+// in registers; the kernel reads their frozen leaves from the code's mask).
+constexpr int kScFuse = 8;
+
+static void gen_sc_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int o, int S, int side,
+                           std::vector<uint32_t> &ops, int &max_depth)
+{
+    const uint32_t off = (uint32_t)o << 16;
+    int type = classify(c, pr, o, S);
+    if (type) {
+        ops.push_back(op_make(OP_NODE, (uint32_t)d, (uint32_t)type, (uint32_t)side, 0) | off);
+        if (d > max_depth) max_depth = d;
+        return;
+    }
+    if (d >= 1 && S <= kScFuse && subtree_unpruned(c, pr, o, S)) {
+        ops.push_back(op_make(OP_RSUB, (uint32_t)d, 0, (uint32_t)side, 0) | off);
+        if (d > max_depth) max_depth = d;
+        return;
+    }
+    ops.push_back(op_make(OP_F, (uint32_t)d, 0, 0, 0) | off);
+    gen_sc_program(c, pr, d + 1, o, S / 2, 0, ops, max_depth);
+    ops.push_back(op_make(OP_G, (uint32_t)d, 0, 0, 0) | off);
+    gen_sc_program(c, pr, d + 1, o + S / 2, S / 2, 1, ops, max_depth);
+    if (d > 0) ops.push_back(op_make(OP_COMB, (uint32_t)(d + 1), 0, (uint32_t)side, 0) | off);
+}
+
 // Peephole fusion of the schedule: a right register-subtree pair (or quad)
 // directly followed by its parent's h step takes that step over.
 static void fuse_ops(std::vector<uint32_t> &ops)
@@ -476,14 +505,18 @@ static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, bool fixed
     }
     std::vector<uint32_t> ops;
     int max_depth = 0;
-    rc = gen_program(c, eff, fuse, !fixed, 0, 0, c->N, 1, ops, max_depth);
-    if (rc) return rc;
-    if (max_depth > kTabLayers)
+    if (fuse == 0) {
+        gen_sc_program(c, eff, 0, 0, c->N, 1, ops, max_depth);  // the one-path kernel's schedule
+    } else {
+        rc = gen_program(c, eff, fuse, !fixed, 0, 0, c->N, 1, ops, max_depth);
+        if (rc) return rc;
+    }
+    if (fuse != 0 && max_depth > kTabLayers)
         return fail(PSCL_EUNSUPPORTED,
                     "N=%d with register subtrees of %d leaf(s): the schedule reaches depth %d, the kernels' slot "
                     "tables hold %d layers (use subtrees of 2 or more leaves)",
                     c->N, fuse, max_depth, kTabLayers);
-    fuse_ops(ops);
+    if (fuse != 0) fuse_ops(ops);
     Program p;
     p.n_ops = (int)ops.size();
     p.max_depth = max_depth;
@@ -519,7 +552,7 @@ extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
     // the default schedule and every fusion size the code's tuning uses
-    std::vector<int> fuses = {g_fuse_max};
+    std::vector<int> fuses = {g_fuse_max, 0};  // 0: the one-path (SC) kernel's schedule
     {
         std::lock_guard<std::mutex> lk(c->mu);
         for (auto &kv : c->tune) fuses.push_back(kv.second.second);
@@ -617,6 +650,38 @@ static void make_layout(const pscl_code_s *c, const Program &pg, int L, int quan
     lay->gmem_per_warp = (go + 255u) & ~255u;
 }
 
+// Shared-memory slice of the one-path (SC) kernel's warp: the partial-sum
+// bits (N bits), LLR layers 1..max_depth (layer d: N/2^d values), and the
+// info-bit buffer.  Nothing lives in global scratch.
+static void make_sc_layout(const pscl_code_s *c, const Program &pg, int quant, Layout *lay)
+{
+    memset(lay, 0, sizeof(*lay));
+    const int EPW = quant == PSCL_F32 ? 1 : (quant == PSCL_I16 ? 2 : 4);
+    auto align16 = [](uint32_t v) { return (v + 15u) & ~15u; };
+    uint32_t so = 0;
+    lay->bl_off[0] = so;
+    lay->b_words[0] = (uint32_t)(c->N >= 32 ? c->N / 32 : 1);
+    so = align16(so + lay->b_words[0] * 4);
+    for (int d = 1; d <= pg.max_depth; d++) {
+        const int S = c->N >> d;
+        const uint32_t words = (uint32_t)(((S + EPW - 1) / EPW + 3) / 4 * 4);
+        lay->llr_off[d] = so;
+        lay->llr_words[d] = words;
+        lay->llr_smem |= 1u << d;
+        so = align16(so + words * 4);
+    }
+    lay->info_words = (uint32_t)std::max(1, (c->kinfo + 31) / 32);
+    lay->src_off = so;
+    so = align16(so + lay->info_words * 4);
+    lay->smem_per_warp = so;
+    lay->gmem_per_warp = 0;
+}
+
+// one-path stages (SC, the first stage of FA and PA) of batches of up to
+// kScWaves waves of resident warps use the SC kernel
+static bool g_sc_kernel = true;
+constexpr long long kScWaves = 4;
+
 // ---------------------------------------------------------------------------
 // launch plan for one decode call
 struct Plan {
@@ -634,6 +699,11 @@ struct Plan {
     int stages[8];
     size_t budget = 0;         // shared-memory bytes per warp
     int kv = KV_PLAIN;         // decoder kernel variant
+    // one-path stage on the SC kernel (warp per frame, all state on chip)
+    bool sc = false;
+    Program sc_pg;
+    Layout sc_lay;
+    int sc_grid = 0, sc_total_warps = 0;
 };
 
 static const int kWarpsPerBlock = 4;
@@ -717,6 +787,29 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     pl->gmem_scratch = (size_t)max_gmem * (size_t)pl->total_warps;
     pl->list_bytes = pl->n_stages > 1 ? (2 * (size_t)n_frames * 4 + 256 + 255) & ~(size_t)255 : 0;
     pl->total_ws = 256 /* error word + counters */ + pl->list_bytes + pl->gmem_scratch;
+    // a first stage with one path runs on the SC kernel
+    pl->sc = false;
+    if (g_sc_kernel && pl->stages[0] == 1) {
+        rc = build_program ? get_program(c, pr, 0, fixed, &pl->sc_pg) : find_program(c, pr, 0, fixed, &pl->sc_pg);
+        if (rc) return rc;
+        make_sc_layout(c, pl->sc_pg, (int)quant, &pl->sc_lay);
+        int sbps = 0;
+        const size_t sblock = (size_t)pl->sc_lay.smem_per_warp * kWarpsPerBlock;
+        e = sc_attrs((int)quant, sblock, 32 * kWarpsPerBlock, &sbps);
+        if (e != cudaSuccess) return fail(PSCL_ECUDA, "SC kernel attributes: %s", cudaGetErrorString(e));
+        // A warp spends far more instructions per frame than a lane of the
+        // list kernel, which decodes 32 one-path frames per warp side by side,
+        // but it finishes its frame about five times sooner: the SC kernel
+        // takes batches of up to kScWaves waves of resident warps, where it
+        // finishes first; larger batches go to the list kernel.
+        const long long smax = (long long)dp.sms * sbps * kWarpsPerBlock;
+        if (sbps >= 1 && (long long)n_frames <= kScWaves * smax) {
+            const long long sw = n_frames < 1 ? 1 : (n_frames < smax ? n_frames : smax);
+            pl->sc_grid = (int)((sw + kWarpsPerBlock - 1) / kWarpsPerBlock);
+            pl->sc_total_warps = pl->sc_grid * kWarpsPerBlock;
+            pl->sc = true;
+        }
+    }
     return PSCL_OK;
 }
 
@@ -788,8 +881,23 @@ static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_a
             it.next_count = counts + (s & 1);
             CU(cudaMemsetAsync(it.next_count, 0, sizeof(int32_t), stream));
         }
-        const size_t smem = (size_t)it.lay.smem_per_warp * kWarpsPerBlock;
-        cudaError_t e = launch_stage((int)quant, pl.kv, kp, pl.grid, smem, stream);
+        cudaError_t e;
+        if (s == 0 && pl.sc) {
+            // one path: warp per frame, layers and partial sums on chip
+            it.ops = pl.sc_pg.d_ops;
+            it.n_ops = pl.sc_pg.n_ops;
+            it.root_special = pl.sc_pg.root_special;
+            it.lay = pl.sc_lay;
+            kp.smem_per_warp = pl.sc_lay.smem_per_warp;
+            kp.total_warps = pl.sc_total_warps;
+            kp.gmem = nullptr;
+            kp.gmem_per_warp = 0;
+            e = launch_sc((int)quant, kp, pl.sc_grid, 32 * kWarpsPerBlock,
+                          (size_t)pl.sc_lay.smem_per_warp * kWarpsPerBlock, stream);
+        } else {
+            const size_t smem = (size_t)it.lay.smem_per_warp * kWarpsPerBlock;
+            e = launch_stage((int)quant, pl.kv, kp, pl.grid, smem, stream);
+        }
         if (e != cudaSuccess) return fail(PSCL_ECUDA, "decode launch: %s", cudaGetErrorString(e));
         launches++;
     }
@@ -888,6 +996,12 @@ extern "C" int pscl_set_tuning(int target_warps_per_sm)
 {
     if (target_warps_per_sm < 1 || target_warps_per_sm > 64) return fail(PSCL_EINVAL, "target warps per SM out of range");
     g_target_warps_per_sm = target_warps_per_sm;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_set_sc_kernel(int enable)
+{
+    g_sc_kernel = enable != 0;
     return PSCL_OK;
 }
 

@@ -143,6 +143,9 @@ cudaError_t launch_scl_f32(const KParams &p, int kv, int grid, int block, size_t
 cudaError_t launch_scl_i16(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_scl_i8(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t scl_func_attrs(int quant, int kv, size_t smem, int block, int *blocks_per_sm);
+// the one-path (SC) kernel: warp per frame, single item (sc_kernel.cu)
+cudaError_t launch_sc(int quant, const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t sc_attrs(int quant, size_t smem, int block, int *blocks_per_sm);
 
 // ---------------------------------------------------------------------------
 // serving loop (server.cu)

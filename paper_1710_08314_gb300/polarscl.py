@@ -109,6 +109,7 @@ def lib() -> C.CDLL:
             L.pscl_debug_error_word.argtypes = [C.POINTER(u32)]
             L.pscl_set_tuning.argtypes = [i]
             L.pscl_set_fusion.argtypes = [i]
+            L.pscl_set_sc_kernel.argtypes = [i]
             _libs[v] = L
             # optional process-wide tuning overrides (the autotuner sets these per call)
             if os.environ.get("PSCL_WARPS_PER_SM"):
@@ -229,6 +230,10 @@ def pscl_set_tuning(target_warps_per_sm: int):
 
 def pscl_set_fusion(max_leaves: int):
     return _check(lib().pscl_set_fusion(int(max_leaves)))
+
+
+def pscl_set_sc_kernel(enable: bool):
+    return _check(lib().pscl_set_sc_kernel(1 if enable else 0))
 
 
 # ---------------------------------------------------------------------------

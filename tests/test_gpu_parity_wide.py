@@ -179,3 +179,28 @@ def test_custom_crcs_and_density_evolution_codes(pool, name):
         ref = pool.decode(code, llr, 8, oracle.CASCL, QMAP[quant][1], p)
         bad = compare(got, ref)
         assert not bad, describe(got, ref, bad[0])
+
+
+@pytest.mark.parametrize("name", ["c1_cascl_128_64_L4", "u09", "u43", "c2_2048_1723", "ln_8192_4096", "crc6_512_256"])
+@pytest.mark.parametrize("quant", ["f32", "i16", "i8"])
+@pytest.mark.parametrize("prune", [None, "all"])
+def test_sc_kernel_equals_the_oracle_and_the_list_kernel(pool, name, quant, prune):
+    """One-path decoding (SC) on the warp-per-frame kernel and on the list
+    kernel: identical bits, status and metric, equal to the oracle."""
+    from paper_1710_08314_gb300 import polarscl as ps, pruning
+    d = synth.load_code(name)
+    p = None if prune is None else dict(mask=15, rep_max=8 if quant == "i8" else 0, spc_max=4, r1_t=2, spc_t=4)
+    gp = pruning(**p) if p else None
+    n = 300 if d["N"] <= 2048 else 64
+    code, _, llr = make_inputs(d, n, 1.0 if d["N"] < 2048 else 3.0, 990)
+    g = gpu_code(d)
+    a = gpu_decode(g, llr, 1, "sc", quant, gp)
+    ps.pscl_set_sc_kernel(False)
+    try:
+        b = gpu_decode(g, llr, 1, "sc", quant, gp)
+    finally:
+        ps.pscl_set_sc_kernel(True)
+    assert not compare(a, b), "SC kernel and list kernel differ"
+    o = pool.decode(code, llr, 1, oracle.SC, QMAP[quant][1], p)
+    bad = compare(a, o)
+    assert not bad, describe(a, o, bad[0])
