@@ -189,57 +189,83 @@ struct ScFrame {
         }
     }
 
-    // a node of up to 8 positions: every lane reads all of them (one shared
-    // load serves the whole warp) and takes the same decision, so no lane
-    // has to wait for another
-    __device__ void node_small(int d, int o, int S, int type, V &pm)
+    // the S (<= 8) values of a depth-d node, read by every lane (one shared
+    // load serves the whole warp)
+    template <int S>
+    __device__ void load_small(int d, V (&a)[S]) const
     {
-        V a[8];
+        constexpr int NW = (S + Qt::EPW - 1) / Qt::EPW;
+        if (d == 0) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = i < S ? elem(d, i) : Qt::zero();
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t wd = word0(w);
+#pragma unroll
+                for (int e = 0; e < Qt::EPW; ++e)
+                    if (w * Qt::EPW + e < S) a[w * Qt::EPW + e] = Qt::elem(wd, e);
+            }
+        } else {
+            const uint32_t *in = layer(d);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t wd = in[w];
+#pragma unroll
+                for (int e = 0; e < Qt::EPW; ++e)
+                    if (w * Qt::EPW + e < S) a[w * Qt::EPW + e] = Qt::elem(wd, e);
+            }
+        }
+    }
+
+    // a node of S <= 8 positions: every lane reads all of them and takes the
+    // same decision, so no lane has to wait for another
+    template <int S>
+    __device__ void node_small(int d, int o, int type, V &pm)
+    {
+        V a[S];
+        load_small<S>(d, a);
         uint32_t h = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) h |= (uint32_t)(i < S && a[i] < 0) << i;
+        for (int i = 0; i < S; ++i) h |= (uint32_t)(a[i] < 0) << i;
         if (type == NT_R1) {
             put_small(o, S, h);
-            return;
-        }
-        if (type == NT_R0 || type == NT_REP) {
+        } else if (type == NT_R0) {
+            if (!Qt::FIXED) {
+                TreeSum<Qt> t0;
+                V p0 = Qt::zero();
+#pragma unroll
+                for (int i = 0; i < S; ++i) p0 = t0.push(a[i] < 0 ? Qt::absv(a[i]) : Qt::zero(), i);
+                pm = Qt::add(pm, p0);
+            }
+            put_small(o, S, 0u);
+        } else if (type == NT_REP) {
             TreeSum<Qt> t0, t1;
             V p0 = Qt::zero(), p1 = Qt::zero();
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (i < S) {
-                    p0 = t0.push(a[i] < 0 ? Qt::absv(a[i]) : Qt::zero(), i);
-                    p1 = t1.push(a[i] > 0 ? Qt::absv(a[i]) : Qt::zero(), i);
-                }
-            if (type == NT_R0) {
-                if (!Qt::FIXED) pm = Qt::add(pm, p0);
-                put_small(o, S, 0u);
-                return;
+            for (int i = 0; i < S; ++i) {
+                p0 = t0.push(a[i] < 0 ? Qt::absv(a[i]) : Qt::zero(), i);
+                p1 = t1.push(a[i] > 0 ? Qt::absv(a[i]) : Qt::zero(), i);
             }
             const V c0 = Qt::add(Qt::FIXED ? Qt::zero() : pm, p0), c1 = Qt::add(Qt::FIXED ? Qt::zero() : pm, p1);
             const bool ones = Qt::key(c1) < Qt::key(c0);
             if (!Qt::FIXED) pm = ones ? c1 : c0;
             put_small(o, S, ones ? 0xFFFFFFFFu : 0u);
-            return;
-        }
-        // SPC: odd parity flips the least reliable position (smallest (|a|, i))
-        if (__popc(h) & 1) {
-            int r0 = 0;
-            uint32_t kb = Qt::key(Qt::absv(a[0]));
+        } else {
+            // SPC: odd parity flips the least reliable position (smallest (|a|, i))
+            if (__popc(h) & 1) {
+                int r0 = 0;
+                uint32_t kb = Qt::key(Qt::absv(a[0]));
 #pragma unroll
-            for (int i = 1; i < 8; ++i) {
-                const uint32_t k = Qt::key(Qt::absv(a[i]));
-                if (i < S && k < kb) {
-                    kb = k;
-                    r0 = i;
+                for (int i = 1; i < S; ++i) {
+                    const uint32_t k = Qt::key(Qt::absv(a[i]));
+                    if (k < kb) {
+                        kb = k;
+                        r0 = i;
+                    }
                 }
+                h ^= 1u << r0;
+                if (!Qt::FIXED) pm = Qt::add(pm, Qt::add(Qt::zero(), Qt::from_key(kb)));
             }
-            h ^= 1u << r0;
-            if (!Qt::FIXED) pm = Qt::add(pm, Qt::add(Qt::zero(), Qt::from_key(kb)));
+            put_small(o, S, h);
         }
-        put_small(o, S, h);
     }
 
     // an unpruned subtree of S leaves (S = 2, 4, 8) decoded in registers by
@@ -272,8 +298,7 @@ struct ScFrame {
     __device__ void rsub_step(int d, int o, V &pm)
     {
         V a[S];
-#pragma unroll
-        for (int i = 0; i < S; ++i) a[i] = elem(d, i);
+        load_small<S>(d, a);
         const uint32_t fz = ~(__ldg(&P.code.amask[o >> 5]) >> (o & 31));
         put_small(o, S, rsub<S>(a, fz, pm));
     }
@@ -282,9 +307,12 @@ struct ScFrame {
     __device__ void node(int d, int o, int type, V &pm)
     {
         const int S = N >> d;
-        if (S <= 8) {
-            node_small(d, o, S, type, pm);
-            return;
+        switch (S) {
+        case 1: node_small<1>(d, o, type, pm); return;
+        case 2: node_small<2>(d, o, type, pm); return;
+        case 4: node_small<4>(d, o, type, pm); return;
+        case 8: node_small<8>(d, o, type, pm); return;
+        default: break;
         }
         if (type == NT_R0) {
             const V pen = tree_sum(d, S, [](V a) { return a < 0 ? Qt::absv(a) : Qt::zero(); });
