@@ -752,7 +752,7 @@ def run_study(name):
         out["results"] = run_lsweep(gen, snrs=(1.0, 1.5, 2.0, 2.5, 3.0), frames=1 << 18)
         print(json.dumps(out), flush=True)
         return
-    target, fine = 1e-4, 2_000_000
+    target, fine = 1e-4, 1_000_000
     res = {}
     for n in (256, 1024, 4096):
         for rn in ("13", "12", "23"):
@@ -968,7 +968,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": "Mb/s", "h2d_bytes_per_step": int(llr.numel() * 4),
                 "d2h_bytes_per_step": int(info_out.numel() + status.numel() * 4)},
         "gpu_launches": launches_per_step * args.steps,
-        "tuning": {"warps_per_sm": tuning[0], "fuse_leaves": tuning[1], "measured_now": measured},
+        "tuning": {"warps_per_sm": tuning[0], "fuse_leaves": tuning[1], "warps_per_block": tuning[2],
+                   "measured_now": measured},
         "roofline": roof,
         "clocks": clocks,
         "fer": fer, "crc_fail_rate": crc_fail,

@@ -118,10 +118,13 @@ int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
  * else = the pruned entry): warps_per_sm (1..32) sizes each warp's shared-memory
  * slice (more warps hide more latency, fewer keep more LLR layers on chip);
  * fuse_leaves (1, 2, 4, 8) is the largest unpruned subtree decoded in
- * registers.  (0, 0) restores the defaults (28 warps, 8 leaves).  Results
- * never depend on the tuning.  Written by the package's autotuner.         */
+ * registers; warps_per_block (1, 2, 4, 8; 0 = 4) sets the frames a block
+ * holds (warps x 32/L) and so the granularity of shared-memory allocation
+ * and of block scheduling.  (0, 0, 0) restores the defaults (28 warps, 8
+ * leaves, 4 warps per block).  Results never depend on the tuning.  Written
+ * by the package's autotuner.                                               */
 int pscl_code_tune(pscl_code code, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
-                   int fuse_leaves);
+                   int fuse_leaves, int warps_per_block);
 
 /* Decode n_frames frames (Algorithm 1 with the selected algorithm).
  * llr: device, n_frames x (N - P) float32, row-major.

@@ -1,13 +1,16 @@
-"""Autotuner for the decoder's two schedule knobs, measured on the GPU.
+"""Autotuner for the decoder's launch and schedule knobs, measured on the GPU.
 
 For a code, list size, number format and pruning setting it times decodes of
 a sample batch over a grid of
   - resident warps per SM (which sizes each warp's shared-memory slice: more
     warps hide more latency, fewer keep more LLR layers on chip), and
   - the largest unpruned subtree decoded in registers (node fusion),
-keeps the fastest, applies it to the code (pscl_code_tune) and stores it in a
-JSON cache keyed by the GPU model and a digest of the code, so later runs
-reuse it without measuring.  Results never depend on the tuning; only time.
+then, at the best pair, over the warps per block (frames per block =
+warps x 32/L: the granularity of shared-memory allocation and of block
+scheduling); keeps the fastest, applies it to the code (pscl_code_tune) and
+stores it in a JSON cache keyed by the GPU model and a digest of the code, so
+later runs reuse it without measuring (PSCL_RETUNE=1 measures again).
+Results never depend on the tuning; only time.
 """
 from __future__ import annotations
 
@@ -22,6 +25,7 @@ DEFAULT_CACHE = os.environ.get(
     "PSCL_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json"))
 WARPS_GRID = (8, 12, 16, 20, 24, 28)
 FUSE_GRID = (2, 4, 8)
+BLOCK_GRID = (2, 4, 8)
 _lock = threading.Lock()
 
 
@@ -62,26 +66,36 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE) -> None:
 
 
 def measure(code, llr, L, quant, prune=None, algo=ps.PSCL_CASCL, warps_grid=WARPS_GRID, fuse_grid=FUSE_GRID,
-            reps=3):
-    """Time every (warps per SM, fusion) pair on the sample LLRs; returns the
-    list of results (ms per decode) and the best pair."""
+            block_grid=BLOCK_GRID, reps=3):
+    """Time every (warps per SM, fusion) pair on the sample LLRs, then the
+    warps per block at the best pair; returns the list of results (ms per
+    decode) and the best setting."""
     import torch
     n = int(llr.shape[0])
     info = torch.empty((n, code.nbytes), dtype=torch.uint8, device=llr.device)
     status = torch.empty((n,), dtype=torch.int32, device=llr.device)
     results = []
+
+    def run(w, f, b):
+        ps.pscl_code_tune(code.handle, L, quant, w, f, prune, b)
+        ps.pscl_prepare(code.handle, prune)
+        ps.pscl_decode(code.handle, llr, n, L, algo, prune, quant, info, status, None, None)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ps.pscl_decode(code.handle, llr, n, L, algo, prune, quant, info, status, None, None)
+        e1.record()
+        torch.cuda.synchronize()
+        results.append(dict(warps_per_sm=w, fuse=f, warps_per_block=b, ms=e0.elapsed_time(e1) / reps))
+
     for w in warps_grid:
         for f in fuse_grid:
-            ps.pscl_code_tune(code.handle, L, quant, w, f, prune)
-            ps.pscl_decode(code.handle, llr, n, L, algo, prune, quant, info, status, None, None)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                ps.pscl_decode(code.handle, llr, n, L, algo, prune, quant, info, status, None, None)
-            e1.record()
-            torch.cuda.synchronize()
-            results.append(dict(warps_per_sm=w, fuse=f, ms=e0.elapsed_time(e1) / reps))
+            run(w, f, 4)
+    best = min(results, key=lambda r: r["ms"])
+    for b in block_grid:
+        if b != 4:
+            run(best["warps_per_sm"], best["fuse"], b)
     best = min(results, key=lambda r: r["ms"])
     return results, best
 
@@ -95,21 +109,24 @@ def tuned(code, L, quant, llr_sample=None, prune=None, algo=ps.PSCL_CASCL, path:
     with _lock:
         cache = load_cache(path)
     hit = cache.get(key)
+    remeasure = remeasure or os.environ.get("PSCL_RETUNE", "0") == "1"
     if hit and not remeasure:
-        ps.pscl_code_tune(code.handle, L, quant, hit["warps_per_sm"], hit["fuse"], prune)
+        wpb = hit.get("warps_per_block", 4)
+        ps.pscl_code_tune(code.handle, L, quant, hit["warps_per_sm"], hit["fuse"], prune, wpb)
         ps.pscl_prepare(code.handle, prune)  # schedules for the tuned fusion size
-        return (hit["warps_per_sm"], hit["fuse"]), False
+        return (hit["warps_per_sm"], hit["fuse"], wpb), False
     if llr_sample is None:
         return None, False
     results, best = measure(code, llr_sample, L, quant, prune, algo)
-    ps.pscl_code_tune(code.handle, L, quant, best["warps_per_sm"], best["fuse"], prune)
+    ps.pscl_code_tune(code.handle, L, quant, best["warps_per_sm"], best["fuse"], prune, best["warps_per_block"])
     ps.pscl_prepare(code.handle, prune)
     with _lock:
         cache = load_cache(path)
-        cache[key] = dict(warps_per_sm=best["warps_per_sm"], fuse=best["fuse"], ms=best["ms"],
+        cache[key] = dict(warps_per_sm=best["warps_per_sm"], fuse=best["fuse"],
+                          warps_per_block=best["warps_per_block"], ms=best["ms"],
                           frames=int(llr_sample.shape[0]), grid=results)
         try:
             save_cache(cache, path)
         except OSError:
             pass
-    return (best["warps_per_sm"], best["fuse"]), True
+    return (best["warps_per_sm"], best["fuse"], best["warps_per_block"]), True

@@ -135,6 +135,13 @@ struct Program {
     int root_special = 0;
 };
 
+// measured tuning of one (list size, number format, pruning) of a code
+struct Tuning {
+    int warps_per_sm = 0;     // resident warps per SM the shared-memory slices are sized for
+    int fuse = 0;             // largest register subtree (leaves)
+    int warps_per_block = 0;  // warps of a block (frames per block = warps x 32/L)
+};
+
 struct pscl_code_s {
     int dev = -1;
     int N = 0, n = 0, K = 0, kinfo = 0, crc_len = 0, P = 0, systematic = 1;
@@ -145,7 +152,7 @@ struct pscl_code_s {
     std::mutex mu;
     std::map<std::vector<int>, Program> programs;
     // measured tuning per (list size, number format): warps per SM, fusion size
-    std::map<int, std::pair<int, int>> tune;
+    std::map<int, Tuning> tune;
 };
 
 static uint32_t crc_poly32(int c, uint32_t poly)
@@ -345,15 +352,19 @@ static int tune_key(int L, int quant, const pscl_pruning *pr)
     return L * 8 + quant + ((pr && pr->mask) ? 1024 : 0);
 }
 
-static void tuning_for(pscl_code c, int L, int quant, const pscl_pruning *pr, int *wps, int *fuse)
+static const int kWarpsPerBlock = 4;  // default warps per block
+
+static void tuning_for(pscl_code c, int L, int quant, const pscl_pruning *pr, int *wps, int *fuse, int *wpb = nullptr)
 {
     *wps = g_target_warps_per_sm;
     *fuse = g_fuse_max;
+    if (wpb) *wpb = kWarpsPerBlock;
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->tune.find(tune_key(L, quant, pr));
     if (it != c->tune.end()) {
-        *wps = it->second.first;
-        *fuse = it->second.second;
+        *wps = it->second.warps_per_sm;
+        *fuse = it->second.fuse;
+        if (wpb && it->second.warps_per_block > 0) *wpb = it->second.warps_per_block;
     }
 }
 
@@ -555,7 +566,7 @@ extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
     std::vector<int> fuses = {g_fuse_max, 0};  // 0: the one-path (SC) kernel's schedule
     {
         std::lock_guard<std::mutex> lk(c->mu);
-        for (auto &kv : c->tune) fuses.push_back(kv.second.second);
+        for (auto &kv : c->tune) fuses.push_back(kv.second.fuse);
     }
     for (int f : fuses)
         for (int fixed = 0; fixed < 2; ++fixed) {
@@ -567,7 +578,7 @@ extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
 }
 
 extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
-                              int fuse_leaves)
+                              int fuse_leaves, int warps_per_block)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
     if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return fail(PSCL_EINVAL, "L=%d", L);
@@ -580,7 +591,14 @@ extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, const pscl_p
     if (warps_per_sm < 1 || warps_per_sm > 32) return fail(PSCL_EINVAL, "warps per SM %d out of 1..32", warps_per_sm);
     if (fuse_leaves != 1 && fuse_leaves != 2 && fuse_leaves != 4 && fuse_leaves != 8)
         return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8", fuse_leaves);
-    c->tune[tune_key(L, (int)quant, pruning)] = std::make_pair(warps_per_sm, fuse_leaves);
+    if (warps_per_block != 0 && warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 &&
+        warps_per_block != 8)
+        return fail(PSCL_EINVAL, "warps per block %d: must be 1, 2, 4 or 8 (0 = default)", warps_per_block);
+    Tuning t;
+    t.warps_per_sm = warps_per_sm;
+    t.fuse = fuse_leaves;
+    t.warps_per_block = warps_per_block;
+    c->tune[tune_key(L, (int)quant, pruning)] = t;
     return PSCL_OK;
 }
 
@@ -706,18 +724,16 @@ struct Plan {
     int sc_grid = 0, sc_total_warps = 0;
 };
 
-static const int kWarpsPerBlock = 4;
-
-// shared-memory bytes per warp when wps warps (in blocks of four) share an
+// shared-memory bytes per warp when wps warps (in blocks of wpb) share an
 // SM: each block gets an equal share of the SM's shared memory, less the
 // runtime's per-block reservation, rounded down to the 128-byte allocation
-// unit, split over its four warps
-static size_t slice_budget(const DevProps &dp, int wps)
+// unit, split over its warps
+static size_t slice_budget(const DevProps &dp, int wps, int wpb = kWarpsPerBlock)
 {
-    const int blocks = (wps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int blocks = (wps + wpb - 1) / wpb;
     const long long per_block = (long long)dp.smem_per_sm / blocks - dp.smem_reserved;
-    size_t budget = per_block > 0 ? ((size_t)per_block & ~(size_t)127) / kWarpsPerBlock : 0;
-    if (budget > (size_t)dp.smem_optin / kWarpsPerBlock) budget = (size_t)dp.smem_optin / kWarpsPerBlock;
+    size_t budget = per_block > 0 ? ((size_t)per_block & ~(size_t)127) / wpb : 0;
+    if (budget > (size_t)dp.smem_optin / wpb) budget = (size_t)dp.smem_optin / wpb;
     return budget & ~(size_t)15;
 }
 
@@ -733,8 +749,9 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     int dev;
     CU(cudaGetDevice(&dev));
     if (dev != c->dev) return fail(PSCL_EINVAL, "code was created on device %d, current device is %d", c->dev, dev);
-    int wps, fuse;
-    tuning_for(c, L, (int)quant, pr, &wps, &fuse);
+    int wps, fuse, wpb;
+    tuning_for(c, L, (int)quant, pr, &wps, &fuse, &wpb);
+    pl->warps_per_block = wpb;
     const bool fixed = quant != PSCL_F32;
     int rc = build_program ? get_program(c, pr, fuse, fixed, &pl->pg) : find_program(c, pr, fuse, fixed, &pl->pg);
     if (rc) return rc;
@@ -756,7 +773,7 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     // every stage uses the same per-warp slices (the layout of the smallest
     // list size needs the most layer-0 room, the largest the most paths:
     // both only depend on N, EPW and 32/L for layer 0)
-    const size_t budget = slice_budget(dp, wps);
+    const size_t budget = slice_budget(dp, wps, wpb);
     pl->budget = budget;
     // each stage recomputes its own layout at launch; the plan keeps maxima
     uint32_t max_smem = 0, max_gmem = 0;
@@ -766,13 +783,13 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
         if (l.smem_per_warp > max_smem) max_smem = l.smem_per_warp;
         if (l.gmem_per_warp > max_gmem) max_gmem = l.gmem_per_warp;
     }
-    pl->smem_block = (size_t)max_smem * kWarpsPerBlock;
+    pl->smem_block = (size_t)max_smem * wpb;
     int bps = 0;
     pl->kv = kernel_variant(pl->pg.has_nodes != 0, wps);
-    cudaError_t e = scl_func_attrs((int)quant, pl->kv, pl->smem_block, 32 * kWarpsPerBlock, &bps);
+    cudaError_t e = scl_func_attrs((int)quant, pl->kv, pl->smem_block, 32 * wpb, &bps);
     if (e != cudaSuccess) return fail(PSCL_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     if (bps < 1) return fail(PSCL_EUNSUPPORTED, "no block fits (shared memory %zu bytes)", pl->smem_block);
-    const int max_warps = dp.sms * bps * kWarpsPerBlock;
+    const int max_warps = dp.sms * bps * wpb;
     const int fpw_min = 32 / pl->stages[pl->n_stages - 1];
     long long tasks = ((long long)n_frames + fpw_min - 1) / fpw_min;
     long long want = tasks < 1 ? 1 : tasks;
@@ -781,8 +798,8 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     long long tasks0 = ((long long)n_frames + (32 / pl->stages[0]) - 1) / (32 / pl->stages[0]);
     if (tasks0 > want) want = tasks0;
     int tw = (int)(want < max_warps ? want : max_warps);
-    pl->grid = (tw + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    pl->total_warps = pl->grid * kWarpsPerBlock;
+    pl->grid = (tw + wpb - 1) / wpb;
+    pl->total_warps = pl->grid * wpb;
     pl->gmem_per_warp = max_gmem;
     pl->gmem_scratch = (size_t)max_gmem * (size_t)pl->total_warps;
     pl->list_bytes = pl->n_stages > 1 ? (2 * (size_t)n_frames * 4 + 256 + 255) & ~(size_t)255 : 0;
@@ -824,11 +841,12 @@ extern "C" int pscl_workspace_size(pscl_code c, int n_frames, int L, pscl_algo a
     return PSCL_OK;
 }
 
-static cudaError_t launch_stage(int quant, int kv, const KParams &kp, int grid, size_t smem, cudaStream_t s)
+static cudaError_t launch_stage(int quant, int kv, const KParams &kp, int grid, size_t smem, cudaStream_t s,
+                                int wpb = kWarpsPerBlock)
 {
-    if (quant == PSCL_F32) return launch_scl_f32(kp, kv, grid, 32 * kWarpsPerBlock, smem, s);
-    if (quant == PSCL_I16) return launch_scl_i16(kp, kv, grid, 32 * kWarpsPerBlock, smem, s);
-    return launch_scl_i8(kp, kv, grid, 32 * kWarpsPerBlock, smem, s);
+    if (quant == PSCL_F32) return launch_scl_f32(kp, kv, grid, 32 * wpb, smem, s);
+    if (quant == PSCL_I16) return launch_scl_i16(kp, kv, grid, 32 * wpb, smem, s);
+    return launch_scl_i8(kp, kv, grid, 32 * wpb, smem, s);
 }
 
 static int g_last_launches = 0;
@@ -895,8 +913,8 @@ static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_a
             e = launch_sc((int)quant, kp, pl.sc_grid, 32 * kWarpsPerBlock,
                           (size_t)pl.sc_lay.smem_per_warp * kWarpsPerBlock, stream);
         } else {
-            const size_t smem = (size_t)it.lay.smem_per_warp * kWarpsPerBlock;
-            e = launch_stage((int)quant, pl.kv, kp, pl.grid, smem, stream);
+            const size_t smem = (size_t)it.lay.smem_per_warp * pl.warps_per_block;
+            e = launch_stage((int)quant, pl.kv, kp, pl.grid, smem, stream, pl.warps_per_block);
         }
         if (e != cudaSuccess) return fail(PSCL_ECUDA, "decode launch: %s", cudaGetErrorString(e));
         launches++;
@@ -1068,17 +1086,17 @@ extern "C" int pscl_decode_static(pscl_code c, const float *llr, int n_frames, i
     // frame lists bound what can be decoded
     const size_t fixed = 256 + pl.list_bytes;
     const size_t per_warp = pl.total_warps ? pl.gmem_scratch / (size_t)pl.total_warps : 0;
-    if (fixed + (size_t)kWarpsPerBlock * per_warp > PSCL_STATIC_SCRATCH_BYTES)
+    const int wpb = pl.warps_per_block;
+    if (fixed + (size_t)wpb * per_warp > PSCL_STATIC_SCRATCH_BYTES)
         return fail(PSCL_EINVAL,
                     "pscl_decode_static: needs %zu bytes of scratch (%zu for frame lists, %zu per warp x %d) "
                     "but its static scratch holds %u bytes",
-                    fixed + (size_t)kWarpsPerBlock * per_warp, pl.list_bytes, per_warp, kWarpsPerBlock,
-                    PSCL_STATIC_SCRATCH_BYTES);
+                    fixed + (size_t)wpb * per_warp, pl.list_bytes, per_warp, wpb, PSCL_STATIC_SCRATCH_BYTES);
     if (per_warp > 0) {
         size_t fit = (PSCL_STATIC_SCRATCH_BYTES - fixed) / per_warp;
         if (fit < (size_t)pl.total_warps) {
-            pl.total_warps = (int)(fit / kWarpsPerBlock) * kWarpsPerBlock;
-            pl.grid = pl.total_warps / kWarpsPerBlock;
+            pl.total_warps = (int)(fit / wpb) * wpb;
+            pl.grid = pl.total_warps / wpb;
             pl.gmem_scratch = per_warp * (size_t)pl.total_warps;
             pl.total_ws = fixed + pl.gmem_scratch;
         }

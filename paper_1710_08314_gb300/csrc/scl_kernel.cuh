@@ -1426,10 +1426,12 @@ __device__ __forceinline__ void load_item(Ctx &c, const Item *src, const KParams
 // (uneven batches) the next task comes from a device counter, so warps that
 // drew short frames take more of them; otherwise warps stride over the
 // frames of the single item.
-// MINB blocks of four warps per SM bound the registers: the node-capable
-// variant runs 4 (128 registers), the node-free one 5 (96) or 7 (72)
+// The registers are capped as for MINB blocks of four warps per SM: the
+// node-capable variant as for 4 (128 registers), the node-free one as for 5
+// (96) or 7 (72).  The cap does not fix the block size: blocks of 1, 2, 4
+// or 8 warps (frames per block, a tuned knob) all fit it.
 template <class Qt, bool NODES, int MINB>
-__global__ void __launch_bounds__(128, MINB) scl_kernel(const __grid_constant__ KParams K)
+__global__ void __maxnreg__((65536 / (128 * MINB)) & ~7) scl_kernel(const __grid_constant__ KParams K)
 {
     extern __shared__ __align__(16) char smem[];
     Ctx c;

@@ -87,7 +87,7 @@ def lib() -> C.CDLL:
             L.pscl_decode_ws.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp, C.c_size_t, vp]
             L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
             L.pscl_decode_static.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
-            L.pscl_code_tune.argtypes = [vp, i, i, vp, i, i]
+            L.pscl_code_tune.argtypes = [vp, i, i, vp, i, i, i]
             L.pscl_server_start.argtypes = [vp, C.POINTER(vp)]
             L.pscl_server_submit.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
             L.pscl_server_poll.argtypes = [vp, vp, i, C.POINTER(i)]
@@ -172,9 +172,9 @@ def pscl_code_info(code):
     return N.value, K.value, Ki.value, P.value
 
 
-def pscl_code_tune(code, L, quant, warps_per_sm, fuse_leaves, prune=None):
+def pscl_code_tune(code, L, quant, warps_per_sm, fuse_leaves, prune=None, warps_per_block=0):
     return _check(lib().pscl_code_tune(code, L, quant, C.byref(prune) if prune is not None else None,
-                                       warps_per_sm, fuse_leaves))
+                                       warps_per_sm, fuse_leaves, warps_per_block))
 
 
 def pscl_prepare(code, prune=None):
