@@ -36,10 +36,15 @@ ALGO_CASCL = 1
 QUANT = {"f32": 0, "i16": 1, "i8": 2}
 
 
-def headline_config(quant: str = "f32", batch: int = BATCH, ws: int = 1) -> dict:
-    """The workload both arms report (the driver compares the two lines)."""
-    return {"workload": f"CA-SCL (2048,1723 incl. CRC-32) L=32 {quant} unpruned, BPSK-AWGN "
-                        f"{EBN0_DB} dB, GA frozen set at 4.5 dB",
+ALGO_NAMES = {"cascl": "CA-SCL", "sc": "SC", "fascl": "FA-SSCL"}
+
+
+def headline_config(quant: str = "f32", batch: int = BATCH, ws: int = 1, algo: str = "cascl",
+                    pruned: bool = False) -> dict:
+    """The workload both arms report (the driver compares the two lines);
+    --algo / --pruned select another decode of the same frames (profiling)."""
+    return {"workload": f"{ALGO_NAMES[algo]} (2048,1723 incl. CRC-32) L=32 {quant} "
+                        f"{'pruned' if pruned else 'unpruned'}, BPSK-AWGN {EBN0_DB} dB, GA frozen set at 4.5 dB",
             "frames_per_step": batch, "l2": "inputs larger than L2 (134 MB LLRs per step)",
             "parallelism": f"replicas x{ws}"}
 
@@ -835,6 +840,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true", help="skip the further workloads")
     ap.add_argument("--study", choices=["spc4plus", "lsweep"], help="run one study instead (one JSON line)")
+    ap.add_argument("--algo", default="cascl", choices=list(ALGO_NAMES),
+                    help="decode of the timed step (default: the metric's CA-SCL)")
+    ap.add_argument("--pruned", action="store_true", help="R0/R1/REP/SPC4 tree pruning in the timed step")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -865,6 +873,9 @@ def main():
     code = Code(d["frozen"], d["crc_len"], d["crc_poly"], d["punct"], d["systematic"])
     B, K_info = args.batch, code.K_info
     quant = QUANT[args.quant]
+    from paper_1710_08314_gb300 import pruning as _pruning
+    ALGO = {"cascl": ALGO_CASCL, "sc": 0, "fascl": 3}[args.algo]
+    PRUNE = _pruning(15, rep_max=8 if args.quant == "i8" else 0) if args.pruned else None
     # synthetic inputs (resident in HBM): bits -> library encoder -> channel
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1234 + rank)
@@ -875,12 +886,12 @@ def main():
     # schedule knobs from the autotuner (cached per GPU model and code)
     from paper_1710_08314_gb300 import autotune
     log("headline: tuning")
-    tuning, measured = autotune.tuned(code, L_LIST, quant, llr[:8192].contiguous())
+    tuning, measured = autotune.tuned(code, L_LIST, quant, llr[:8192].contiguous(), prune=PRUNE, algo=ALGO)
     log(f"headline: tuned {tuning}, timing")
     cur = {"llr": llr}
 
     def step():
-        ps.pscl_decode(code.handle, cur["llr"], B, L_LIST, ALGO_CASCL, None, quant, info_out, status, None, stream)
+        ps.pscl_decode(code.handle, cur["llr"], B, L_LIST, ALGO, PRUNE, quant, info_out, status, None, stream)
 
     for _ in range(args.warmup):
         step()
@@ -923,7 +934,7 @@ def main():
 
     def e2e_step():
         llr_d.copy_(llr_h, non_blocking=True)
-        ps.pscl_decode(code.handle, llr_d, B, L_LIST, ALGO_CASCL, None, quant, info_out, status, None, stream)
+        ps.pscl_decode(code.handle, llr_d, B, L_LIST, ALGO, PRUNE, quant, info_out, status, None, stream)
         info_h.copy_(info_out, non_blocking=True)
         status_h.copy_(status, non_blocking=True)
 
@@ -932,7 +943,7 @@ def main():
     torch.cuda.synchronize()
     _, e2e_ms = timed_steps(e2e_step, args.steps, stream, dist)
     e2e_value = frames_all * K_info / (max_over_ranks(e2e_ms) / 1e3) / 1e6
-    frame_ms = frame_latency(code, llr[:1], L_LIST, ALGO_CASCL, None, quant)
+    frame_ms = frame_latency(code, llr[:1], L_LIST, ALGO, PRUNE, quant)
 
     if rank != 0:
         if dist:
@@ -942,7 +953,8 @@ def main():
     # rooflines of the decode kernel: algorithmic f/g updates per frame (the
     # oracle's count for this code and L) over the measured launch time
     wpath = os.path.join(ROOT, "tests", "golden", "work_per_frame.json")
-    work = json.load(open(wpath)).get(f"{WORKLOAD}_L{L_LIST}_unpruned") if os.path.exists(wpath) else None
+    wkey = f"{WORKLOAD}_L{1 if args.algo == 'sc' else L_LIST}_{'pruned' if args.pruned else 'unpruned'}"
+    work = json.load(open(wpath)).get(wkey) if os.path.exists(wpath) and args.algo != "fascl" else None
     clocks = clk.summary()
     peaks = measured_peaks()
     avg_launch_s = (sum(per_launch_ms) / len(per_launch_ms)) / 1e3 / max(1, launches_per_step)
@@ -950,7 +962,8 @@ def main():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = clocks.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1440.0
     if work:
-        prof = profile_figures() if args.quant == "f32" and B >= 4096 else {}
+        prof = profile_figures() if args.quant == "f32" and B >= 4096 and args.algo == "cascl" \
+            and not args.pruned else {}
         models = roofline_models(work["fg_elems"], B, avg_launch_s, args.quant, mhz, sms, peaks.get("hbm_gbs"), prof)
         sm = models["smem"]
         roof = {"bound": "smem", "achieved": sm["achieved"], "peak": sm["peak"], "unit": "GB/s", "frac": sm["frac"],
@@ -964,7 +977,7 @@ def main():
         "value": value, "unit": "Mb/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.quant, "data": "synthetic",
-        "config": headline_config(args.quant, B, ws),
+        "config": headline_config(args.quant, B, ws, args.algo, args.pruned),
         "e2e": {"value": e2e_value, "unit": "Mb/s", "h2d_bytes_per_step": int(llr.numel() * 4),
                 "d2h_bytes_per_step": int(info_out.numel() + status.numel() * 4)},
         "gpu_launches": launches_per_step * args.steps,
