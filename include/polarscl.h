@@ -73,7 +73,11 @@ typedef enum { PSCL_F32 = 0, PSCL_I16 = 1, PSCL_I8 = 2 } pscl_quant;
  * only), 0 = no limit (SPC4+).  r1_max: 0 = no limit.  r1_t / spc_t: how many
  * least-reliable positions the R1 / SPC candidates flip (r1_t = 2 is the
  * paper's Chase-2, Sec. IV-C); the kernels accept 1 <= r1_t <= 3 and
- * 1 <= spc_t <= 4.  mask = 0 decodes the full tree leaf by leaf.            */
+ * 1 <= spc_t <= 4.  node_min: the smallest node of two or more leaves that
+ * is pruned (0, 1 or 2 = any size, the paper's setting); smaller nodes are
+ * decoded leaf by leaf, where the GPU decodes them inside its register
+ * subtrees (node_min = 2 x fusion size + 1 keeps every register subtree
+ * whole).  mask = 0 decodes the full tree leaf by leaf.                    */
 typedef struct {
     uint32_t mask;
     int rep_max;
@@ -81,6 +85,7 @@ typedef struct {
     int r1_t;
     int spc_t;
     int r1_max;
+    int node_min;
 } pscl_pruning;
 
 /* Create a code descriptor and upload it to the current CUDA device.

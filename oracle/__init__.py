@@ -34,7 +34,7 @@ class _Code(C.Structure):
 
 class _Pruning(C.Structure):
     _fields_ = [("mask", C.c_uint32), ("rep_max", C.c_int), ("spc_max", C.c_int),
-                ("r1_t", C.c_int), ("spc_t", C.c_int), ("r1_max", C.c_int)]
+                ("r1_t", C.c_int), ("spc_t", C.c_int), ("r1_max", C.c_int), ("node_min", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -108,8 +108,8 @@ class Code:
         return C.byref(self._c)
 
 
-def pruning(mask=0, rep_max=0, spc_max=4, r1_t=2, spc_t=4, r1_max=0):
-    return _Pruning(mask, rep_max, spc_max, r1_t, spc_t, r1_max)
+def pruning(mask=0, rep_max=0, spc_max=4, r1_t=2, spc_t=4, r1_max=0, node_min=0):
+    return _Pruning(mask, rep_max, spc_max, r1_t, spc_t, r1_max, node_min)
 
 
 def polar_transform(v):

@@ -557,13 +557,14 @@ static double tree_sum(const arith_t *A, const double *v, int lo, int hi)
 /* Node classification for tree pruning (Sec. II-B, Sec. III-B-2): the
  * top-most node whose leaves match a type that is enabled and within its size
  * limit replaces its subtree.  Precedence R0 > R1 > REP > SPC.  A size-1 node
- * is a frozen leaf (R0) or an information leaf (R1 of size 1).              */
+ * is a frozen leaf (R0) or an information leaf (R1 of size 1).  Nodes below
+ * node_min leaves are internal: their subtrees are decoded leaf by leaf.   */
 static int classify(const orc_code *cd, const orc_pruning *pr, int o, int S)
 {
     int nf = 0;
     for (int i = o; i < o + S; i++) nf += cd->frozen[i] ? 1 : 0;
     if (S == 1) return nf ? ORC_NODE_R0 : ORC_NODE_R1;
-    if (!pr) return ORC_NODE_INTERNAL;
+    if (!pr || S < pr->node_min) return ORC_NODE_INTERNAL;
     if (nf == S && (pr->mask & ORC_PRUNE_R0)) return ORC_NODE_R0;
     if (nf == 0 && (pr->mask & ORC_PRUNE_R1) && (pr->r1_max == 0 || S <= pr->r1_max))
         return ORC_NODE_R1;

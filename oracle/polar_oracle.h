@@ -21,7 +21,9 @@ typedef struct {
 enum { ORC_PRUNE_R0 = 1, ORC_PRUNE_R1 = 2, ORC_PRUNE_REP = 4, ORC_PRUNE_SPC = 8 };
 
 /* tree pruning: enabled node types, size limits (0 = none; spc_max = 4 is
- * SPC4, rep_max = 8 is REP8-), and flip depths (0 = every position)       */
+ * SPC4, rep_max = 8 is REP8-), flip depths (0 = every position), and the
+ * smallest node of more than one leaf that is pruned (0, 1 or 2 = any;
+ * smaller nodes are decoded leaf by leaf)                                  */
 typedef struct {
     uint32_t mask;
     int rep_max;
@@ -29,6 +31,7 @@ typedef struct {
     int r1_t;
     int spc_t;
     int r1_max;
+    int node_min;
 } orc_pruning;
 
 enum { ORC_NODE_INTERNAL = 0, ORC_NODE_R0 = 1, ORC_NODE_R1 = 2, ORC_NODE_REP = 3, ORC_NODE_SPC = 4 };

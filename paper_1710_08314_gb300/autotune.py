@@ -45,7 +45,8 @@ def code_digest(code) -> str:
 
 def cache_key(code, L, quant, prune, algo=ps.PSCL_CASCL) -> str:
     pk = "none" if prune is None or prune.mask == 0 else (
-        f"{prune.mask}-{prune.rep_max}-{prune.spc_max}-{prune.r1_t}-{prune.spc_t}-{prune.r1_max}")
+        f"{prune.mask}-{prune.rep_max}-{prune.spc_max}-{prune.r1_t}-{prune.spc_t}-{prune.r1_max}"
+        + (f"-m{prune.node_min}" if prune.node_min > 2 else ""))
     return f"{gpu_name()}|N{code.N}|K{code.K}|P{code.P}|{code_digest(code)}|L{L}|q{quant}|a{algo}|{pk}"
 
 

@@ -324,13 +324,14 @@ extern "C" int pscl_code_info(pscl_code c, int *N, int *K, int *K_info, int *n_p
 // node schedule (Sec. II-B tree pruning): pre-order traversal of Algorithm 1;
 // a node whose leaves are all frozen (R0), all information (R1), all frozen
 // but the last (REP) or only the first frozen (SPC) becomes one step when its
-// type is enabled and within its size limit, the top-most such node winning.
+// type is enabled and within its size limits, the top-most such node winning;
+// nodes below node_min leaves are decoded leaf by leaf.
 static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
 {
     int nf = 0;
     for (int i = o; i < o + S; i++) nf += c->frozen[i];
     if (S == 1) return nf ? NT_R0 : NT_R1;
-    if (!pr) return 0;
+    if (!pr || S < pr->node_min) return 0;
     if (nf == S && (pr->mask & PSCL_PRUNE_R0)) return NT_R0;
     if (nf == 0 && (pr->mask & PSCL_PRUNE_R1) && (pr->r1_max == 0 || S <= pr->r1_max)) return NT_R1;
     if (nf == S - 1 && !c->frozen[o + S - 1] && (pr->mask & PSCL_PRUNE_REP) && (pr->rep_max == 0 || S <= pr->rep_max))
@@ -486,14 +487,15 @@ static void fuse_ops(std::vector<uint32_t> &ops)
 static std::vector<int> prune_key(const pscl_pruning *pr, int fuse, bool fixed)
 {
     if (!pr || pr->mask == 0) return {fuse, fixed ? 1 : 0, 0};
-    return {fuse, fixed ? 1 : 0, (int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max};
+    return {fuse, fixed ? 1 : 0, (int)pr->mask, pr->rep_max, pr->spc_max, pr->r1_t, pr->spc_t, pr->r1_max,
+            pr->node_min};
 }
 
 static int check_pruning(const pscl_pruning *pr)
 {
     if (!pr || pr->mask == 0) return PSCL_OK;
     if (pr->mask & ~15u) return fail(PSCL_EINVAL, "pruning mask 0x%x has unknown bits", pr->mask);
-    if (pr->rep_max < 0 || pr->spc_max < 0 || pr->r1_max < 0)
+    if (pr->rep_max < 0 || pr->spc_max < 0 || pr->r1_max < 0 || pr->node_min < 0)
         return fail(PSCL_EINVAL, "negative pruning size limit");
     if ((pr->mask & PSCL_PRUNE_R1) && (pr->r1_t < 1 || pr->r1_t > 3))
         return fail(PSCL_EUNSUPPORTED, "r1_t=%d: the kernels support 1..3", pr->r1_t);

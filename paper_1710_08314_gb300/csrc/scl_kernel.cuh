@@ -466,7 +466,7 @@ __device__ __forceinline__ void normalise(Ctx &c, typename Qt::V &pm)
 
 // Bitonic sort (ascending) of the L*M keys of a segment; element e = slot*M + m.
 template <int M>
-__device__ __forceinline__ void bitonic_seg(uint64_t (&k)[M], int L, int slot)
+__device__ __forceinline__ void bitonic_seg(uint32_t (&k)[M], int L, int slot)
 {
     const int E = L * M;
     for (int size = 2; size <= E; size <<= 1) {
@@ -478,11 +478,8 @@ __device__ __forceinline__ void bitonic_seg(uint64_t (&k)[M], int L, int slot)
                 for (int m = 0; m < M; ++m) {
                     const int e = slot * M + m;
                     const bool up = (e & size) == 0;
-                    uint64_t o = shfl64_xor(k[m], ls);
-                    const bool takemin = lower == up;
-                    uint64_t mn = o < k[m] ? o : k[m];
-                    uint64_t mx = o < k[m] ? k[m] : o;
-                    k[m] = takemin ? mn : mx;
+                    const uint32_t o = __shfl_xor_sync(PSCL_FULL, k[m], ls);
+                    k[m] = lower == up ? min(o, k[m]) : max(o, k[m]);
                 }
             } else {
 #pragma unroll
@@ -494,11 +491,9 @@ __device__ __forceinline__ void bitonic_seg(uint64_t (&k)[M], int L, int slot)
                                 const int mp = m | (1 << sb);
                                 const int e = slot * M + m;
                                 const bool up = (e & size) == 0;
-                                uint64_t a = k[m], b = k[mp];
-                                if ((a > b) == up) {
-                                    k[m] = b;
-                                    k[mp] = a;
-                                }
+                                const uint32_t lo = min(k[m], k[mp]), hi = max(k[m], k[mp]);
+                                k[m] = up ? lo : hi;
+                                k[mp] = up ? hi : lo;
                             }
                         }
                     }
@@ -511,15 +506,19 @@ __device__ __forceinline__ void bitonic_seg(uint64_t (&k)[M], int L, int slot)
 // Keep the min(L, n_active*M) smallest (PM, c) candidates, c = slot*M + m,
 // and give them new slots in increasing c.  kp[m] is the ordered bit pattern
 // of candidate m's metric.  On return, lanes with slot < n_keep know their
-// parent slot, candidate index and metric key.
-template <int M>
+// parent slot, candidate index and metric key.  The L-th smallest metric
+// value tau is found first (float: a 32-bit bitonic network of the keys;
+// fixed point: bisection on the metric's bits with ballot counts); every
+// candidate below tau survives, and of those equal to tau the first in
+// candidate order fill the remaining places.
+template <int M, int VBITS>
 __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], int &par, int &cand,
                                              uint32_t &newkey, int &n_keep, bool &ident)
 {
     ident = false;
-    const int na = c.n_active;
+    const int na = c.n_active, L = c.L;
     const int n_cand = na * M;
-    if (n_cand <= c.L) {
+    if (n_cand <= L) {
         n_keep = n_cand;
         par = c.slot < n_keep ? c.slot / M : 0;
         cand = c.slot < n_keep ? c.slot % M : 0;
@@ -532,8 +531,8 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
         newkey = v;
         return;
     }
-    n_keep = c.L;
-    if (na == c.L) {
+    n_keep = L;
+    if (na == L) {
         // every path's first candidate ranks before every other candidate:
         // the first candidates survive in place, nothing is sorted
         uint32_t mn = 0xFFFFFFFFu;
@@ -549,31 +548,51 @@ __device__ __forceinline__ void select_paths(Ctx &c, const uint32_t (&kp)[M], in
             return;
         }
     }
-    uint64_t k[M];
+    const uint32_t segmask = L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << c.seg);
+    uint32_t a[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m)
-        k[m] = c.slot < na ? (((uint64_t)kp[m] << 32) | (uint32_t)(c.slot * M + m)) : ~0ull;
-    bitonic_seg<M>(k, c.L, c.slot);
-    const int tp = (c.L - 1) / M, tm = (c.L - 1) % M;
-    uint64_t mine = 0;
+    for (int m = 0; m < M; ++m) a[m] = c.slot < na ? kp[m] : 0xFFFFFFFFu;
+    uint32_t tau;
+    if constexpr (VBITS > 0) {
+        uint32_t v = 0;
+#pragma unroll 1
+        for (int bit = VBITS - 1; bit >= 0; --bit) {
+            const uint32_t cv = v | ((1u << bit) - 1u);
+            int cnt = 0;
 #pragma unroll
-    for (int m = 0; m < M; ++m)
-        if (m == tm) mine = k[m];
-    const uint64_t tau = shfl64(mine, c.seg + tp);
-    int cnt = 0;
-    bool surv[M];
+            for (int m = 0; m < M; ++m) cnt += __popc(__ballot_sync(PSCL_FULL, a[m] <= cv) & segmask);
+            if (cnt < L) v |= 1u << bit;
+        }
+        tau = v;
+    } else {
+        uint32_t k[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) k[m] = a[m];
+        bitonic_seg<M>(k, L, c.slot);
+        const int tp = (L - 1) / M, tm = (L - 1) % M;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+            if (m == tm) mine = k[m];
+        tau = __shfl_sync(PSCL_FULL, mine, c.seg + tp);
+    }
+    const uint32_t lt = ((1u << c.lane) - 1u) & segmask;
+    int n_less = 0, eq_rank = 0;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        uint64_t orig = c.slot < na ? (((uint64_t)kp[m] << 32) | (uint32_t)(c.slot * M + m)) : ~0ull;
-        surv[m] = orig <= tau;
-        cnt += surv[m] ? 1 : 0;
+        n_less += __popc(__ballot_sync(PSCL_FULL, a[m] < tau) & segmask);
+        eq_rank += __popc(__ballot_sync(PSCL_FULL, a[m] == tau) & lt);
     }
-    int incl = cnt;
-    for (int off = 1; off < c.L; off <<= 1) {
-        int y = __shfl_up_sync(PSCL_FULL, incl, off, c.L);
-        if (c.slot >= off) incl += y;
+    const int need = L - n_less;
+    bool surv[M];
+    int r = 0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const bool eq = a[m] == tau;
+        surv[m] = a[m] < tau || (eq && eq_rank < need);
+        eq_rank += eq ? 1 : 0;
+        r += __popc(__ballot_sync(PSCL_FULL, surv[m]) & lt);
     }
-    int r = incl - cnt;
     uint32_t *src = (uint32_t *)(c.sm + c.P->lay.src_off);
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -742,7 +761,7 @@ __device__ __forceinline__ void node_select_finish(Ctx &c, int d, int type, int 
     uint32_t newkey;
     bool ident;
     if constexpr (M == 2) select_m2<Qt::VBITS, true>(c, kp[0], kp[1], par, cand, newkey, n_keep, ident);
-    else select_paths<M>(c, kp, par, cand, newkey, n_keep, ident);
+    else select_paths<M, Qt::VBITS>(c, kp, par, cand, newkey, n_keep, ident);
     const int pl = c.seg + par;
     uint32_t hp = h, r0 = rp[0], r1 = rp[1], r2 = rp[2];
     if (!ident) {

@@ -22,11 +22,11 @@ QUANTS = {"f32": PSCL_F32, "i16": PSCL_I16, "i8": PSCL_I8}
 
 class pscl_pruning(C.Structure):
     _fields_ = [("mask", C.c_uint32), ("rep_max", C.c_int), ("spc_max", C.c_int),
-                ("r1_t", C.c_int), ("spc_t", C.c_int), ("r1_max", C.c_int)]
+                ("r1_t", C.c_int), ("spc_t", C.c_int), ("r1_max", C.c_int), ("node_min", C.c_int)]
 
 
-def pruning(mask=0, rep_max=0, spc_max=4, r1_t=2, spc_t=4, r1_max=0) -> pscl_pruning:
-    return pscl_pruning(mask, rep_max, spc_max, r1_t, spc_t, r1_max)
+def pruning(mask=0, rep_max=0, spc_max=4, r1_t=2, spc_t=4, r1_max=0, node_min=0) -> pscl_pruning:
+    return pscl_pruning(mask, rep_max, spc_max, r1_t, spc_t, r1_max, node_min)
 
 
 class pscl_work_item(C.Structure):

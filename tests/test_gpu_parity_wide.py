@@ -204,3 +204,34 @@ def test_sc_kernel_equals_the_oracle_and_the_list_kernel(pool, name, quant, prun
     o = pool.decode(code, llr, 1, oracle.SC, QMAP[quant][1], p)
     bad = compare(a, o)
     assert not bad, describe(a, o, bad[0])
+
+
+@pytest.mark.parametrize("quant", ["f32", "i16", "i8"])
+@pytest.mark.parametrize("node_min", [9, 17])
+@pytest.mark.parametrize("name,L,algo", [("c3_1024_512_L8", 8, "cascl"), (HEADLINE, 32, "cascl"),
+                                         (HEADLINE, 32, "fascl")])
+def test_node_size_minimum(pool, quant, node_min, name, L, algo):
+    """Pruning restricted to nodes of node_min leaves or more: the smaller
+    nodes are decoded leaf by leaf inside the register subtrees."""
+    from paper_1710_08314_gb300 import pruning
+    d = synth.load_code(name)
+    p = dict(mask=15, rep_max=8 if quant == "i8" else 0, spc_max=0, r1_t=2, spc_t=4, node_min=node_min)
+    n = 96 if d["N"] == 2048 else 250
+    code, _, llr = make_inputs(d, n, 1.5 if d["N"] < 2048 else 3.5, 1000 + node_min + L)
+    g = gpu_decode(gpu_code(d), llr, L, algo, quant, pruning(**p))
+    o = pool.decode(code, llr, L, AMAP[algo][1], QMAP[quant][1], p)
+    bad = compare(g, o)
+    assert not bad, describe(g, o, bad[0])
+
+
+def test_node_minimum_above_every_node_is_the_unpruned_decoder():
+    """With node_min above N nothing is pruned: the schedule, the kernel and
+    every output equal the unpruned decode's."""
+    from paper_1710_08314_gb300 import pruning
+    d = synth.load_code(HEADLINE)
+    _, _, llr = make_inputs(d, 512, 3.5, 1100)
+    g = gpu_code(d)
+    a = gpu_decode(g, llr, 32, "cascl", "f32", None)
+    b = gpu_decode(g, llr, 32, "cascl", "f32", pruning(15, rep_max=0, node_min=4096))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
