@@ -982,7 +982,7 @@ def main():
                 "d2h_bytes_per_step": int(info_out.numel() + status.numel() * 4)},
         "gpu_launches": launches_per_step * args.steps,
         "tuning": {"warps_per_sm": tuning[0], "fuse_leaves": tuning[1], "warps_per_block": tuning[2],
-                   "measured_now": measured},
+                   "resident_warps": tuning[3] or tuning[0], "measured_now": measured},
         "roofline": roof,
         "clocks": clocks,
         "fer": fer, "crc_fail_rate": crc_fail,

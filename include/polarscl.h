@@ -120,16 +120,21 @@ int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
 
 /* Record measured tuning for decodes of this code with list size L, number
  * format quant and pruning (NULL or mask 0 = the unpruned entry, anything
- * else = the pruned entry): warps_per_sm (1..32) sizes each warp's shared-memory
- * slice (more warps hide more latency, fewer keep more LLR layers on chip);
+ * else = the pruned entry): warps_per_sm (1..64) sizes each warp's shared-memory
+ * slice as if that many warps shared an SM (more warps hide more latency,
+ * fewer keep more LLR layers on chip; sizing for more warps than are
+ * resident leaves the rest of the SM's shared memory to the L1 cache);
  * fuse_leaves (1, 2, 4, 8) is the largest unpruned subtree decoded in
  * registers; warps_per_block (1, 2, 4, 8; 0 = 4) sets the frames a block
  * holds (warps x 32/L) and so the granularity of shared-memory allocation
- * and of block scheduling.  (0, 0, 0) restores the defaults (28 warps, 8
- * leaves, 4 warps per block).  Results never depend on the tuning.  Written
- * by the package's autotuner.                                               */
+ * and of block scheduling; resident_warps (0..64; 0 = warps_per_sm) picks
+ * the decoder's register cap: 24 or more selects the 72-register variant
+ * (up to 28 warps per SM), less the 96-register (node-free, 20 warps) or
+ * 128-register (node-capable, 16 warps) one.  (0, 0, 0, 0) restores the
+ * defaults (28 warps, 8 leaves, 4 warps per block).  Results never depend
+ * on the tuning.  Written by the package's autotuner.                      */
 int pscl_code_tune(pscl_code code, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
-                   int fuse_leaves, int warps_per_block);
+                   int fuse_leaves, int warps_per_block, int resident_warps);
 
 /* Decode n_frames frames (Algorithm 1 with the selected algorithm).
  * llr: device, n_frames x (N - P) float32, row-major.
@@ -359,6 +364,15 @@ int pscl_debug_server_exit(pscl_server s, int *warp, long long *idle_ns, unsigne
 int pscl_debug_server_slots(pscl_server s, uint64_t *claim, uint32_t *done, int32_t *nframes, uint64_t *tickets);
 int pscl_debug_error_word(uint32_t *out);
 int pscl_debug_checked(void);
+/* pscl_debug_step_cycles: in the step-profiling build (PSCL_OPPROF=1, built
+ * as libpolarscl_opprof.so), the list kernel's lane 0 of every warp adds the
+ * SM cycles of each schedule step to a per-device counter by category: out
+ * receives 16 (cycles, steps) pairs, categories 0..6 the opcodes F, G, leaf
+ * or node, h, register subtree, register-subtree pair, 16-leaf quad; 7 + the
+ * node type (8 R0, 9 R1, 10 REP, 11 SPC) for pruned nodes; 12 loading a
+ * task's frames; 13 the final CRC selection and output.  reset != 0 zeroes
+ * the counters after reading.  Other builds return PSCL_EUNSUPPORTED.       */
+int pscl_debug_step_cycles(uint64_t *out, int reset);
 
 /* Message for the calling thread's most recent error ("" if none).         */
 const char *pscl_last_error(void);

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
-UNITS = ["api.cu", "scl_f32.cu", "scl_i16.cu", "scl_i8.cu", "scl_attrs.cu", "encode.cu", "server.cu", "server_nodes.cu",
+UNITS = ["api.cu", "scl_f32.cu", "scl_i16.cu", "scl_i8.cu", "scl_f32_nodes.cu", "scl_i16_nodes.cu",
+         "scl_i8_nodes.cu", "scl_attrs.cu", "encode.cu", "server.cu", "server_nodes.cu",
          "sc_kernel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -53,6 +54,8 @@ def build(variant: str = "release", force: bool = False, verbose: bool = False) 
              "-I", os.path.join(ROOT, "include")] + ARCH
     if variant == "checked":
         flags.append("-DPSCL_CHECKED")
+    elif variant == "opprof":
+        flags.append("-DPSCL_OPPROF")
     if verbose:
         flags += ["-Xptxas", "-v"]
 

@@ -137,9 +137,10 @@ struct Program {
 
 // measured tuning of one (list size, number format, pruning) of a code
 struct Tuning {
-    int warps_per_sm = 0;     // resident warps per SM the shared-memory slices are sized for
+    int warps_per_sm = 0;     // warps per SM the shared-memory slices are sized for
     int fuse = 0;             // largest register subtree (leaves)
     int warps_per_block = 0;  // warps of a block (frames per block = warps x 32/L)
+    int resident_warps = 0;   // occupancy target selecting the register cap (0 = warps_per_sm)
 };
 
 struct pscl_code_s {
@@ -355,17 +356,20 @@ static int tune_key(int L, int quant, const pscl_pruning *pr)
 
 static const int kWarpsPerBlock = 4;  // default warps per block
 
-static void tuning_for(pscl_code c, int L, int quant, const pscl_pruning *pr, int *wps, int *fuse, int *wpb = nullptr)
+static void tuning_for(pscl_code c, int L, int quant, const pscl_pruning *pr, int *wps, int *fuse, int *wpb = nullptr,
+                       int *res = nullptr)
 {
     *wps = g_target_warps_per_sm;
     *fuse = g_fuse_max;
     if (wpb) *wpb = kWarpsPerBlock;
+    if (res) *res = g_target_warps_per_sm;
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->tune.find(tune_key(L, quant, pr));
     if (it != c->tune.end()) {
         *wps = it->second.warps_per_sm;
         *fuse = it->second.fuse;
         if (wpb && it->second.warps_per_block > 0) *wpb = it->second.warps_per_block;
+        if (res) *res = it->second.resident_warps > 0 ? it->second.resident_warps : it->second.warps_per_sm;
     }
 }
 
@@ -580,7 +584,7 @@ extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
 }
 
 extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
-                              int fuse_leaves, int warps_per_block)
+                              int fuse_leaves, int warps_per_block, int resident_warps)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
     if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return fail(PSCL_EINVAL, "L=%d", L);
@@ -590,7 +594,9 @@ extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, const pscl_p
         c->tune.erase(tune_key(L, (int)quant, pruning));
         return PSCL_OK;
     }
-    if (warps_per_sm < 1 || warps_per_sm > 32) return fail(PSCL_EINVAL, "warps per SM %d out of 1..32", warps_per_sm);
+    if (warps_per_sm < 1 || warps_per_sm > 64) return fail(PSCL_EINVAL, "warps per SM %d out of 1..64", warps_per_sm);
+    if (resident_warps < 0 || resident_warps > 64)
+        return fail(PSCL_EINVAL, "resident warps %d out of 0..64", resident_warps);
     if (fuse_leaves != 1 && fuse_leaves != 2 && fuse_leaves != 4 && fuse_leaves != 8)
         return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8", fuse_leaves);
     if (warps_per_block != 0 && warps_per_block != 1 && warps_per_block != 2 && warps_per_block != 4 &&
@@ -600,6 +606,7 @@ extern "C" int pscl_code_tune(pscl_code c, int L, pscl_quant quant, const pscl_p
     t.warps_per_sm = warps_per_sm;
     t.fuse = fuse_leaves;
     t.warps_per_block = warps_per_block;
+    t.resident_warps = resident_warps;
     c->tune[tune_key(L, (int)quant, pruning)] = t;
     return PSCL_OK;
 }
@@ -751,8 +758,8 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     int dev;
     CU(cudaGetDevice(&dev));
     if (dev != c->dev) return fail(PSCL_EINVAL, "code was created on device %d, current device is %d", c->dev, dev);
-    int wps, fuse, wpb;
-    tuning_for(c, L, (int)quant, pr, &wps, &fuse, &wpb);
+    int wps, fuse, wpb, res;
+    tuning_for(c, L, (int)quant, pr, &wps, &fuse, &wpb, &res);
     pl->warps_per_block = wpb;
     const bool fixed = quant != PSCL_F32;
     int rc = build_program ? get_program(c, pr, fuse, fixed, &pl->pg) : find_program(c, pr, fuse, fixed, &pl->pg);
@@ -787,7 +794,7 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
     }
     pl->smem_block = (size_t)max_smem * wpb;
     int bps = 0;
-    pl->kv = kernel_variant(pl->pg.has_nodes != 0, wps);
+    pl->kv = kernel_variant(pl->pg.has_nodes != 0, res);
     cudaError_t e = scl_func_attrs((int)quant, pl->kv, pl->smem_block, 32 * wpb, &bps);
     if (e != cudaSuccess) return fail(PSCL_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     if (bps < 1) return fail(PSCL_EUNSUPPORTED, "no block fits (shared memory %zu bytes)", pl->smem_block);
@@ -843,12 +850,35 @@ extern "C" int pscl_workspace_size(pscl_code c, int n_frames, int L, pscl_algo a
     return PSCL_OK;
 }
 
+#ifdef PSCL_OPPROF
+// step-profiling build: one counter block per device, zeroed at allocation
+static std::mutex g_prof_mu;
+static std::map<int, unsigned long long *> g_prof;
+static unsigned long long *prof_buffer()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    auto it = g_prof.find(dev);
+    if (it != g_prof.end()) return it->second;
+    unsigned long long *p = nullptr;
+    if (cudaMalloc(&p, 32 * sizeof(unsigned long long)) != cudaSuccess) return nullptr;
+    cudaMemset(p, 0, 32 * sizeof(unsigned long long));
+    g_prof[dev] = p;
+    return p;
+}
+#endif
+
 static cudaError_t launch_stage(int quant, int kv, const KParams &kp, int grid, size_t smem, cudaStream_t s,
                                 int wpb = kWarpsPerBlock)
 {
-    if (quant == PSCL_F32) return launch_scl_f32(kp, kv, grid, 32 * wpb, smem, s);
-    if (quant == PSCL_I16) return launch_scl_i16(kp, kv, grid, 32 * wpb, smem, s);
-    return launch_scl_i8(kp, kv, grid, 32 * wpb, smem, s);
+#ifdef PSCL_OPPROF
+    KParams kq = kp;
+    kq.op_cycles = prof_buffer();
+    return launch_scl(quant, kv, kq, grid, 32 * wpb, smem, s);
+#else
+    return launch_scl(quant, kv, kp, grid, 32 * wpb, smem, s);
+#endif
 }
 
 static int g_last_launches = 0;
@@ -1031,6 +1061,24 @@ extern "C" int pscl_set_fusion(int max_leaves)
         return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8", max_leaves);
     g_fuse_max = max_leaves;
     return PSCL_OK;
+}
+
+
+extern "C" int pscl_debug_step_cycles(uint64_t *out, int reset)
+{
+#ifdef PSCL_OPPROF
+    if (!out) return fail(PSCL_EINVAL, "out is NULL");
+    unsigned long long *p = prof_buffer();
+    if (!p) return fail(PSCL_ECUDA, "profile counters unavailable");
+    CU(cudaDeviceSynchronize());
+    CU(cudaMemcpy(out, p, 32 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    if (reset) CU(cudaMemset(p, 0, 32 * sizeof(unsigned long long)));
+    return PSCL_OK;
+#else
+    (void)out;
+    (void)reset;
+    return fail(PSCL_EUNSUPPORTED, "not a step-profiling build");
+#endif
 }
 
 extern "C" int pscl_debug_checked(void)

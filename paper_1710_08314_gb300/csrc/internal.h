@@ -127,21 +127,21 @@ struct KParams {
     const float *llr_pool;      // batch pools (items add their offsets)
     uint8_t *info_pool;
     int32_t *status_pool;
+    unsigned long long *op_cycles;  // step-profiling builds: 16 x (cycles, steps); else unused
 };
 
-// launchers, one per number format (defined in scl_*.cu)
-// nodes: the schedule contains pruned nodes (R0/R1/REP/SPC steps)
-// decoder kernel variants: node-free with 5 blocks of 4 warps per SM (96
-// registers), node-capable (4 blocks), node-free with 7 blocks (72 registers,
-// for tunings of 24 or more resident warps per SM)
-enum KernelVariant : int { KV_PLAIN = 0, KV_NODES = 1, KV_DENSE = 2 };
-inline int kernel_variant(bool nodes, int warps_per_sm)
+// decoder kernel variants (scl_<format>.cu, scl_<format>_nodes.cu): without
+// or with the pruned-node handlers, each at a lower occupancy (node-free: 5
+// blocks of 4 warps per SM, 96 registers; node-capable: 4 blocks, 128
+// registers) or a higher one (7 blocks, 72 registers).  resident_warps is the
+// tuned occupancy target: 24 or more selects the higher one.
+enum KernelVariant : int { KV_PLAIN = 0, KV_NODES = 1, KV_DENSE = 2, KV_NODES_DENSE = 3 };
+inline int kernel_variant(bool nodes, int resident_warps)
 {
-    return nodes ? KV_NODES : (warps_per_sm >= 24 ? KV_DENSE : KV_PLAIN);
+    const bool hi = resident_warps >= 24;
+    return nodes ? (hi ? KV_NODES_DENSE : KV_NODES) : (hi ? KV_DENSE : KV_PLAIN);
 }
-cudaError_t launch_scl_f32(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_scl_i16(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_scl_i8(const KParams &p, int kv, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_scl(int quant, int kv, const KParams &p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t scl_func_attrs(int quant, int kv, size_t smem, int block, int *blocks_per_sm);
 // the one-path (SC) kernel: warp per frame, single item (sc_kernel.cu)
 cudaError_t launch_sc(int quant, const KParams &p, int grid, int block, size_t smem, cudaStream_t s);

@@ -154,7 +154,29 @@ struct Ctx {
     const uint32_t *ops;
     int n_ops;
     uint32_t idxL[2], idxS[2];  // per-layer slot tables: layers 1..12, 6 x 5 bits per word
+#ifdef PSCL_OPPROF
+    unsigned long long *prof;   // step-profiling builds: cycle and step counters
+#endif
 };
+
+#ifdef PSCL_OPPROF
+// step-profiling builds: lane 0 adds a step's SM cycles to its category
+// (0..6 opcodes, 7 + node type for OP_NODE, 12 frame loading, 13 the final
+// CRC selection and output)
+__device__ __forceinline__ void prof_add(const Ctx &c, int cat, long long t0)
+{
+    __syncwarp();
+    if (c.lane == 0 && c.prof) {
+        atomicAdd(&c.prof[2 * cat], (unsigned long long)(clock64() - t0));
+        atomicAdd(&c.prof[2 * cat + 1], 1ull);
+    }
+}
+#define PSCL_PROF_T0(v) const long long v = clock64()
+#define PSCL_PROF_ADD(cat, v) prof_add(c, cat, v)
+#else
+#define PSCL_PROF_T0(v)
+#define PSCL_PROF_ADD(cat, v)
+#endif
 
 // slot of layer d (1 <= d <= kTabLayers) in a table
 __device__ __forceinline__ int tab_get(const uint32_t (&t)[2], int d)
@@ -1241,6 +1263,7 @@ template <class Qt, bool NODES>
 __device__ void decode_task(Ctx &c, int pos0, int count)
 {
     typedef typename Qt::V V;
+    PSCL_PROF_T0(t_load);
     const Item &P = *c.P;
     const DevCode &cd = P.code;
     int32_t *fids = (int32_t *)(c.sm + P.lay.src_off) + P.lay.info_words;  // 32 frame ids
@@ -1258,25 +1281,95 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         const uint32_t cap = P.lay.llr_words[0];
         const int rows = (c.N + Qt::EPW - 1) / Qt::EPW;
         const int stride = c.N - cd.P;
-        for (int wi = c.lane; wi < rows * c.fpw; wi += 32) {
-            const int row = wi / c.fpw, fr = wi - row * c.fpw;
-            const int f = fids[fr];
-            uint32_t word = 0;
+        const bool vec = cd.P == 0 && c.N % (4 * Qt::EPW) == 0 && (reinterpret_cast<uintptr_t>(P.llr) & 15u) == 0;
+        if (vec) {
+            // nothing punctured: lane l takes quads of frame l mod (32/L), reads
+            // a quad's 4 x EPW LLRs with 16-byte loads (two quads in flight)
+            // and writes it with one 16-byte store
+            const int totalq = (rows >> 2) * c.fpw;
+            for (int w0 = c.lane; w0 < totalq; w0 += 64) {
+                float v[2][4 * Qt::EPW];
 #pragma unroll
-            for (int e = 0; e < Qt::EPW; ++e) {
-                const int i = row * Qt::EPW + e;
-                float x = 0.0f;
-                if (i < c.N && f >= 0) {
-                    const int col = __ldg(&cd.in_index[i]);
-                    if (col >= 0) {
-                        const float *a = &P.llr[(size_t)f * (size_t)stride + col];
-                        x = P.llr_cg ? __ldcg(a) : __ldg(a);
+                for (int u = 0; u < 2; ++u) {
+                    const int wi = w0 + 32 * u;
+                    const int q = wi / c.fpw, fr = wi - q * c.fpw;
+                    const int f = wi < totalq ? fids[fr] : -1;
+#pragma unroll
+                    for (int e = 0; e < Qt::EPW; ++e) {
+                        float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (f >= 0) {
+                            const float4 *a = reinterpret_cast<const float4 *>(
+                                &P.llr[(size_t)f * (size_t)stride + (size_t)(q * 4 * Qt::EPW + 4 * e)]);
+                            x = P.llr_cg ? __ldcg(a) : __ldg(a);
+                        }
+                        v[u][4 * e] = x.x;
+                        v[u][4 * e + 1] = x.y;
+                        v[u][4 * e + 2] = x.z;
+                        v[u][4 * e + 3] = x.w;
                     }
                 }
-                uint32_t q = Qt::quant(x);
-                word |= Qt::EPW == 1 ? q : (q << (e * Qt::BITS));
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int wi = w0 + 32 * u;
+                    if (wi < totalq) {
+                        const int q = wi / c.fpw, fr = wi - q * c.fpw;
+                        uint32_t w[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            w[k] = 0u;
+#pragma unroll
+                            for (int e = 0; e < Qt::EPW; ++e) {
+                                const uint32_t qv = Qt::quant(v[u][k * Qt::EPW + e]);
+                                w[k] |= Qt::EPW == 1 ? qv : (qv << (e * Qt::BITS));
+                            }
+                        }
+                        const int idx = qa(4 * q, fr, c.fpw);
+                        if (PSCL_OK_IDX(c, idx + 3, cap, 1024u))
+                            *reinterpret_cast<uint4 *>(l0 + idx) = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
+                }
             }
-            st(c, l0, qa(row, fr, c.fpw), cap, word, 1024u);
+        } else {
+            // punctured codes: lane l takes frame l mod (32/L) (its rows in turn,
+            // the positions through the code's input index): each lane has eight
+            // loads in flight before it quantises and stores
+            constexpr int U = 8 / Qt::EPW;
+            const int total = rows * c.fpw;
+            for (int w0 = c.lane; w0 < total; w0 += 32 * U) {
+                float x[U][Qt::EPW];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int wi = w0 + 32 * u;
+                    const int row = wi / c.fpw, fr = wi - row * c.fpw;
+                    const int f = wi < total ? fids[fr] : -1;
+#pragma unroll
+                    for (int e = 0; e < Qt::EPW; ++e) {
+                        const int i = row * Qt::EPW + e;
+                        x[u][e] = 0.0f;
+                        if (f >= 0 && i < c.N) {
+                            const int col = __ldg(&cd.in_index[i]);
+                            if (col >= 0) {
+                                const float *a = &P.llr[(size_t)f * (size_t)stride + col];
+                                x[u][e] = P.llr_cg ? __ldcg(a) : __ldg(a);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int wi = w0 + 32 * u;
+                    if (wi < total) {
+                        const int row = wi / c.fpw, fr = wi - row * c.fpw;
+                        uint32_t word = 0;
+#pragma unroll
+                        for (int e = 0; e < Qt::EPW; ++e) {
+                            const uint32_t q = Qt::quant(x[u][e]);
+                            word |= Qt::EPW == 1 ? q : (q << (e * Qt::BITS));
+                        }
+                        st(c, l0, qa(row, fr, c.fpw), cap, word, 1024u);
+                    }
+                }
+            }
         }
     }
     __syncwarp();
@@ -1284,10 +1377,12 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
     tab_fill(c.idxL, c.slot);
     tab_fill(c.idxS, c.slot);
     V pm = Qt::zero();
+    PSCL_PROF_ADD(12, t_load);
     // walk the node schedule
     for (int i = 0; i < c.n_ops; ++i) {
         const uint32_t op = __ldg(&c.ops[i]);
         const int d = op_depth(op);
+        PSCL_PROF_T0(t_op);
         switch (op_code(op)) {
         case OP_F: op_f<Qt>(c, d); break;
         case OP_G: op_g<Qt>(c, d); break;
@@ -1322,7 +1417,9 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
             break;
         }
         __syncwarp();
+        PSCL_PROF_ADD(op_code(op) == OP_NODE ? 7 + (int)op_type(op) : (int)op_code(op), t_op);
     }
+    PSCL_PROF_T0(t_fin);
     // final selection (Sec. IV-B): best metric among paths passing the CRC
     const int cl = c.seg + tab_get(c.idxS, 1);
     if (!cd.systematic) {
@@ -1398,6 +1495,7 @@ __device__ void decode_task(Ctx &c, int pos0, int count)
         }
     }
     __syncwarp();
+    PSCL_PROF_ADD(13, t_fin);
 }
 
 // copy an item into the warp's shared slice and set the lane roles
@@ -1460,6 +1558,9 @@ __global__ void __maxnreg__((65536 / (128 * MINB)) & ~7) scl_kernel(const __grid
     c.sm = smem + (size_t)warp * K.smem_per_warp;
     c.gm = K.gmem + (size_t)gwarp * K.gmem_per_warp;
     c.P = (const Item *)c.sm;
+#ifdef PSCL_OPPROF
+    c.prof = K.op_cycles;
+#endif
     if (K.tasks == nullptr) {
         load_item(c, &K.single, K, false);
         const Item &it = *c.P;

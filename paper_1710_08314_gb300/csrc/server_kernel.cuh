@@ -130,6 +130,9 @@ __global__ void __launch_bounds__(128, 4) server_kernel(const __grid_constant__ 
     c.sm = smem + (size_t)warp * K.smem_per_warp;
     c.gm = K.gmem + (size_t)gwarp * K.gmem_per_warp;
     c.P = (const Item *)c.sm;
+#ifdef PSCL_OPPROF
+    c.prof = nullptr;
+#endif
     int cur = -1;
     IdleClock idle;
     idle.reset();

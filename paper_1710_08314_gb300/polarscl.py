@@ -66,7 +66,9 @@ _libs: dict[str, C.CDLL] = {}
 
 
 def variant() -> str:
-    return "checked" if os.environ.get("PSCL_CHECKED", "0") == "1" else "release"
+    if os.environ.get("PSCL_CHECKED", "0") == "1":
+        return "checked"
+    return "opprof" if os.environ.get("PSCL_OPPROF", "0") == "1" else "release"
 
 
 def lib() -> C.CDLL:
@@ -87,7 +89,7 @@ def lib() -> C.CDLL:
             L.pscl_decode_ws.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp, C.c_size_t, vp]
             L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
             L.pscl_decode_static.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
-            L.pscl_code_tune.argtypes = [vp, i, i, vp, i, i, i]
+            L.pscl_code_tune.argtypes = [vp, i, i, vp, i, i, i, i]
             L.pscl_server_start.argtypes = [vp, C.POINTER(vp)]
             L.pscl_server_submit.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
             L.pscl_server_poll.argtypes = [vp, vp, i, C.POINTER(i)]
@@ -107,6 +109,7 @@ def lib() -> C.CDLL:
             L.pscl_last_error.restype = C.c_char_p
             L.pscl_version.restype = C.c_char_p
             L.pscl_debug_error_word.argtypes = [C.POINTER(u32)]
+            L.pscl_debug_step_cycles.argtypes = [vp, i]
             L.pscl_set_tuning.argtypes = [i]
             L.pscl_set_fusion.argtypes = [i]
             L.pscl_set_sc_kernel.argtypes = [i]
@@ -172,9 +175,9 @@ def pscl_code_info(code):
     return N.value, K.value, Ki.value, P.value
 
 
-def pscl_code_tune(code, L, quant, warps_per_sm, fuse_leaves, prune=None, warps_per_block=0):
+def pscl_code_tune(code, L, quant, warps_per_sm, fuse_leaves, prune=None, warps_per_block=0, resident_warps=0):
     return _check(lib().pscl_code_tune(code, L, quant, C.byref(prune) if prune is not None else None,
-                                       warps_per_sm, fuse_leaves, warps_per_block))
+                                       warps_per_sm, fuse_leaves, warps_per_block, resident_warps))
 
 
 def pscl_prepare(code, prune=None):
@@ -212,6 +215,18 @@ def pscl_decode_static(code, llr, n_frames, L, algo, prune, quant, info_out, sta
 
 def pscl_encode(code, info, n_frames, x_out, stream=None):
     return _check(lib().pscl_encode(code, _ptr(info), n_frames, _ptr(x_out), _stream(stream)))
+
+
+STEP_CATEGORIES = ("f", "g", "leaf", "h", "rsub", "rsub2", "rsub4", "-", "node_r0", "node_r1", "node_rep",
+                   "node_spc", "load", "final", "-", "-")
+
+
+def pscl_debug_step_cycles(reset=True):
+    """Step-profiling build only: {category: (SM cycles, steps)} summed over
+    the list kernel's warps since the last reset."""
+    out = (C.c_uint64 * 32)()
+    _check(lib().pscl_debug_step_cycles(out, 1 if reset else 0))
+    return {STEP_CATEGORIES[i]: (out[2 * i], out[2 * i + 1]) for i in range(16) if out[2 * i + 1]}
 
 
 def pscl_debug_error_word() -> int:
