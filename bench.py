@@ -40,11 +40,12 @@ ALGO_NAMES = {"cascl": "CA-SCL", "sc": "SC", "fascl": "FA-SSCL"}
 
 
 def headline_config(quant: str = "f32", batch: int = BATCH, ws: int = 1, algo: str = "cascl",
-                    pruned: bool = False) -> dict:
+                    pruned: bool = False, node_min: int = 0) -> dict:
     """The workload both arms report (the driver compares the two lines);
     --algo / --pruned select another decode of the same frames (profiling)."""
+    pn = ("pruned" + (f" (nodes of {node_min}+ leaves)" if node_min > 2 else "")) if pruned else "unpruned"
     return {"workload": f"{ALGO_NAMES[algo]} (2048,1723 incl. CRC-32) L=32 {quant} "
-                        f"{'pruned' if pruned else 'unpruned'}, BPSK-AWGN {EBN0_DB} dB, GA frozen set at 4.5 dB",
+                        f"{pn}, BPSK-AWGN {EBN0_DB} dB, GA frozen set at 4.5 dB",
             "frames_per_step": batch, "l2": "inputs larger than L2 (134 MB LLRs per step)",
             "parallelism": f"replicas x{ws}"}
 
@@ -341,7 +342,9 @@ C2_SNRS = (3.5, 3.75, 4.0, 4.25, 4.5)
 
 def run_c2(gen, snrs=C2_SNRS, frames=1000000):
     """Adaptive FA-SSCL (2048, 1723 incl. CRC-32), Lmax = 32, pruned
-    (R0/R1/REP/SPC4; REP8- for int8), f32 and int8, 10^6 frames per point.
+    (R0/R1/REP/SPC4; REP8- for int8), f32 and int8, 10^6 frames per point;
+    "_n32": the same node types restricted to nodes of 32 or more leaves,
+    SPC of any size (the smaller nodes decoded in register subtrees).
     Per-frame latency as in the paper's Table 3: a frame that stops at list
     size L costs the single-frame decodes of stages 1, 2, ..., L (measured
     one launch per stage); L_avg weighs them by the measured stop histogram,
@@ -352,12 +355,16 @@ def run_c2(gen, snrs=C2_SNRS, frames=1000000):
     d, code = _code("c2_2048_1723")
     out = {}
     Ls = [1, 2, 4, 8, 16, 32]
-    for quant, qn, pr in [(0, "f32", pruning(15, rep_max=0)), (2, "i8", pruning(15, rep_max=8))]:
+    variants = [(0, "f32", "", pruning(15, rep_max=0)), (2, "i8", "", pruning(15, rep_max=8)),
+                (0, "f32", "_n32", pruning(15, rep_max=0, spc_max=0, node_min=17)),
+                (2, "i8", "_n32", pruning(15, rep_max=8, spc_max=0, node_min=17))]
+    for quant, qn, tag, pr in variants:
         stage_ms = None
         for snr in sorted(snrs, reverse=True):
             info, llr = _gen_frames(code, frames, snr, gen)
             if stage_ms is None:
-                autotune.tuned(code, 32, quant, llr[:16384].contiguous(), prune=pr, algo=ps.PSCL_FASCL)
+                # a sample of two waves of the one-path first stage (32 frames per warp)
+                autotune.tuned(code, 32, quant, llr[:1 << 18].contiguous(), prune=pr, algo=ps.PSCL_FASCL)
                 # per-stage single-frame latency (each stage a CA-SCL(L) decode)
                 stage_ms = {L: frame_latency(code, llr[:1], L, ps.PSCL_CASCL if L > 1 else ps.PSCL_SC, pr, quant)
                             for L in Ls}
@@ -372,9 +379,9 @@ def run_c2(gen, snrs=C2_SNRS, frames=1000000):
             cum = {L: sum(stage_ms[l] for l in Ls if l <= L) for L in Ls}
             l_avg = sum(hist[str(L)] * cum[L] for L in Ls) / frames
             bl = batch_latency(_decode_fn(code, llr[:16384], 16384, 32, ps.PSCL_FASCL, pr, quant, o, st))
-            out[f"{qn}_{snr}dB"] = dict(value=frames * code.K_info / ms / 1e3, unit="Mb/s", frames=frames,
-                                        fer=float((o != info).any(dim=1).float().mean()), final_L_hist=hist,
-                                        ms=ms, quant=qn, work="c2_2048_1723_L1_pruned",
+            out[f"{qn}{tag}_{snr}dB"] = dict(value=frames * code.K_info / ms / 1e3, unit="Mb/s", frames=frames,
+                                             fer=float((o != info).any(dim=1).float().mean()), final_L_hist=hist,
+                                             ms=ms, quant=qn, work="c2_2048_1723_L1_pruned" + tag,
                                         latency=dict(frame_avg_ms=l_avg, frame_worst_ms=worst,
                                                      stage_frame_ms={str(L): v for L, v in stage_ms.items()},
                                                      batch16k_p50_ms=bl["batch_p50_ms"],
@@ -389,14 +396,17 @@ C3_SNRS = (1.0, 1.5, 2.0, 2.5, 3.0)
 
 def run_c3(gen, snrs=C3_SNRS, frames=2000000):
     """CA-SCL (1024, 512 incl. CRC-16), L = 8: pruned vs unpruned, int16 and
-    f32, 2x10^6 frames per point."""
+    f32, 2x10^6 frames per point; "pruned_n64": nodes of 64 or more leaves
+    only."""
     import torch
     from paper_1710_08314_gb300 import pruning
     from paper_1710_08314_gb300 import autotune
     d, code = _code("c3_1024_512_L8")
     out = {}
     variants = [("f32", 0, "unpruned", None), ("f32", 0, "pruned", pruning(15, rep_max=0)),
-                ("i16", 1, "unpruned", None), ("i16", 1, "pruned", pruning(15, rep_max=0))]
+                ("f32", 0, "pruned_n64", pruning(15, rep_max=0, node_min=33)),
+                ("i16", 1, "unpruned", None), ("i16", 1, "pruned", pruning(15, rep_max=0)),
+                ("i16", 1, "pruned_n64", pruning(15, rep_max=0, node_min=33))]
     tuned = set()
     for snr in snrs:
         info, llr = _gen_frames(code, frames, snr, gen)
@@ -843,6 +853,7 @@ def main():
     ap.add_argument("--algo", default="cascl", choices=list(ALGO_NAMES),
                     help="decode of the timed step (default: the metric's CA-SCL)")
     ap.add_argument("--pruned", action="store_true", help="R0/R1/REP/SPC4 tree pruning in the timed step")
+    ap.add_argument("--node-min", type=int, default=0, help="with --pruned: smallest pruned node (leaves)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -875,7 +886,7 @@ def main():
     quant = QUANT[args.quant]
     from paper_1710_08314_gb300 import pruning as _pruning
     ALGO = {"cascl": ALGO_CASCL, "sc": 0, "fascl": 3}[args.algo]
-    PRUNE = _pruning(15, rep_max=8 if args.quant == "i8" else 0) if args.pruned else None
+    PRUNE = _pruning(15, rep_max=8 if args.quant == "i8" else 0, node_min=args.node_min) if args.pruned else None
     # synthetic inputs (resident in HBM): bits -> library encoder -> channel
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1234 + rank)
@@ -977,7 +988,7 @@ def main():
         "value": value, "unit": "Mb/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.quant, "data": "synthetic",
-        "config": headline_config(args.quant, B, ws, args.algo, args.pruned),
+        "config": headline_config(args.quant, B, ws, args.algo, args.pruned, args.node_min),
         "e2e": {"value": e2e_value, "unit": "Mb/s", "h2d_bytes_per_step": int(llr.numel() * 4),
                 "d2h_bytes_per_step": int(info_out.numel() + status.numel() * 4)},
         "gpu_launches": launches_per_step * args.steps,
