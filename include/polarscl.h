@@ -370,7 +370,9 @@ int pscl_debug_checked(void);
  * receives 16 (cycles, steps) pairs, categories 0..6 the opcodes F, G, leaf
  * or node, h, register subtree, register-subtree pair, 16-leaf quad; 7 + the
  * node type (8 R0, 9 R1, 10 REP, 11 SPC) for pruned nodes; 12 loading a
- * task's frames; 13 the final CRC selection and output.  reset != 0 zeroes
+ * task's frames; 13 the final CRC selection and output; 14 the two-candidate
+ * selections that took the general (sorting) path, already inside the
+ * categories of their steps.  reset != 0 zeroes
  * the counters after reading.  Other builds return PSCL_EUNSUPPORTED.       */
 int pscl_debug_step_cycles(uint64_t *out, int reset);
 

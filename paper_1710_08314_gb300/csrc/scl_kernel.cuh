@@ -162,7 +162,8 @@ struct Ctx {
 #ifdef PSCL_OPPROF
 // step-profiling builds: lane 0 adds a step's SM cycles to its category
 // (0..6 opcodes, 7 + node type for OP_NODE, 12 frame loading, 13 the final
-// CRC selection and output)
+// CRC selection and output; 14 counts the two-candidate selections that
+// took the general path, inside the steps above)
 __device__ __forceinline__ void prof_add(const Ctx &c, int cat, long long t0)
 {
     __syncwarp();
@@ -760,8 +761,10 @@ __device__ __forceinline__ void select_m2(Ctx &c, uint32_t ka, uint32_t kb, int 
         }
     }
     uint32_t *src = (uint32_t *)(c.sm + c.P->lay.src_off);
+    PSCL_PROF_T0(t_sel);
     const uint64_t r = OUT ? select_m2_general_call<VBITS>(a, b, ka, kb, L, c.lane, c.slot, c.seg, src)
                            : select_m2_general<VBITS>(a, b, ka, kb, L, c.lane, c.slot, c.seg, src);
+    PSCL_PROF_ADD(14, t_sel);
     const uint32_t e0 = (uint32_t)r, e1 = (uint32_t)(r >> 32);
     par = (int)(e0 >> 8) & (L - 1);
     cand = (int)(e0 & 1u);

@@ -218,7 +218,7 @@ def pscl_encode(code, info, n_frames, x_out, stream=None):
 
 
 STEP_CATEGORIES = ("f", "g", "leaf", "h", "rsub", "rsub2", "rsub4", "-", "node_r0", "node_r1", "node_rep",
-                   "node_spc", "load", "final", "-", "-")
+                   "node_spc", "load", "final", "sel2_general", "-")
 
 
 def pscl_debug_step_cycles(reset=True):
