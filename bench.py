@@ -897,14 +897,10 @@ def main():
     # schedule knobs from the autotuner (cached per GPU model and code)
     from paper_1710_08314_gb300 import autotune
     log("headline: tuning")
-    if args.algo == "sc":
-        # the one-path decode runs the list size 1 schedule: tuned as CA-SCL
-        # with L = 1 on a sample of two waves (32 frames per warp)
-        tuning, measured = autotune.tuned(code, 1, quant, llr[:1 << 18].contiguous(), prune=PRUNE,
-                                          algo=ps.PSCL_CASCL)
-    else:
-        sample = llr[:8192] if args.algo == "cascl" else llr[:1 << 18]
-        tuning, measured = autotune.tuned(code, L_LIST, quant, sample.contiguous(), prune=PRUNE, algo=ALGO)
+    # one-path and adaptive decodes start with 32 frames per warp: their
+    # sample covers two waves of those
+    sample = llr[:8192] if args.algo == "cascl" else llr[:1 << 18]
+    tuning, measured = autotune.tuned(code, L_LIST, quant, sample.contiguous(), prune=PRUNE, algo=ALGO)
     log(f"headline: tuned {tuning}, timing")
     cur = {"llr": llr}
 

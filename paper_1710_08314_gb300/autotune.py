@@ -118,11 +118,11 @@ def tuned(code, L, quant, llr_sample=None, prune=None, algo=ps.PSCL_CASCL, path:
           remeasure: bool = False):
     """Apply cached tuning for this (code, L, format, pruning) or measure it on
     llr_sample and cache it.  Returns the applied (warps_per_sm, fuse,
-    warps_per_block, resident_warps) and whether it was measured now.  For
-    the adaptive algorithms the one-path first stage (list size 1, which
-    decodes every frame) is tuned first, as a CA-SCL decode with L = 1."""
-    if algo in (ps.PSCL_FASCL, ps.PSCL_PASCL) and L > 1:
-        tuned(code, 1, quant, llr_sample, prune, ps.PSCL_CASCL, path, remeasure)
+    warps_per_block, resident_warps) and whether it was measured now.  An
+    adaptive or one-path decode runs all its stages with the entry of the
+    list size it is called with, so it is tuned by timing whole decodes of
+    that algorithm (the sample should fill the GPU at the first stage's 32
+    frames per warp)."""
     key = cache_key(code, L, quant, prune, algo)
     with _lock:
         cache = load_cache(path)
