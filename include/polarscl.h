@@ -157,6 +157,26 @@ int pscl_decode(pscl_code code, const float *llr, int n_frames, int L, pscl_algo
                 const pscl_pruning *pruning, pscl_quant quant, uint8_t *info_out,
                 int32_t *status_out, float *pm_out, void *stream);
 
+/* pscl_decode from host buffers, with the transfers overlapped (no
+ * counterpart in the paper: its decoder reads host memory directly).
+ * llr_host: host, n_frames x (N - P) float32, row-major; info_host: host,
+ * n_frames x ceil(K_info / 8) bytes; status_host: host, int32 per frame
+ * (layouts as pscl_decode).  Page-locked host buffers let the copies run
+ * asynchronously; pageable ones work but each copy then waits for itself.
+ * Batches of 8192 frames or more are cut into up to four chunks: one
+ * internal stream copies the chunks in while two others decode them
+ * alternately and copy each chunk's outputs back, so transfers and decodes
+ * of different chunks overlap.  Everything is ordered after the work
+ * already queued on `stream`, and later work on `stream` waits for all of
+ * it: synchronize `stream` before reading the outputs.  The library keeps,
+ * per (device, stream), the internal streams, events and a device staging
+ * buffer (grown on demand; growing waits for that stream's earlier calls).
+ * Not for stream capture.  Errors: as pscl_decode, all argument errors
+ * before anything is enqueued.                                              */
+int pscl_decode_host(pscl_code code, const float *llr_host, int n_frames, int L, pscl_algo algo,
+                     const pscl_pruning *pruning, pscl_quant quant, uint8_t *info_host,
+                     int32_t *status_host, void *stream);
+
 /* Bytes of device workspace pscl_decode_ws needs for this call shape.       */
 int pscl_workspace_size(pscl_code code, int n_frames, int L, pscl_algo algo,
                         const pscl_pruning *pruning, pscl_quant quant, size_t *bytes);

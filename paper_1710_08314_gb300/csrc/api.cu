@@ -960,6 +960,29 @@ static int run_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_a
 // streams never share one
 static std::map<std::pair<int, void *>, std::pair<void *, size_t>> g_ws;
 
+// the library's workspace of (device, stream), grown to at least `bytes`
+static int stream_workspace(int dev, void *stream, size_t bytes, void **ws, size_t *wsb)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto &slot = g_ws[std::make_pair(dev, stream)];
+    if (slot.second < bytes) {
+        if (slot.first) {
+            // only this stream's queued work can still use the old one
+            CU(cudaStreamSynchronize((cudaStream_t)stream));
+            lib_free(slot.first);
+            slot.first = nullptr;
+            slot.second = 0;
+        }
+        size_t want = bytes + bytes / 4;
+        CU(cudaMalloc(&slot.first, want));
+        CU(cudaMemset(slot.first, 0, 256));
+        slot.second = want;
+    }
+    *ws = slot.first;
+    *wsb = slot.second;
+    return PSCL_OK;
+}
+
 extern "C" int pscl_decode(pscl_code c, const float *llr, int n_frames, int L, pscl_algo algo,
                            const pscl_pruning *pr, pscl_quant quant, uint8_t *info_out, int32_t *status_out,
                            float *pm_out, void *stream)
@@ -971,27 +994,109 @@ extern "C" int pscl_decode(pscl_code c, const float *llr, int n_frames, int L, p
     CU(cudaGetDevice(&dev));
     void *ws;
     size_t wsb;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        auto &slot = g_ws[std::make_pair(dev, stream)];
-        if (slot.second < pl.total_ws) {
-            if (slot.first) {
-                // only this stream's queued work can still use the old one
-                CU(cudaStreamSynchronize((cudaStream_t)stream));
-                lib_free(slot.first);
-                slot.first = nullptr;
-                slot.second = 0;
-            }
-            size_t want = pl.total_ws + pl.total_ws / 4;
-            CU(cudaMalloc(&slot.first, want));
-            CU(cudaMemset(slot.first, 0, 256));
-            slot.second = want;
-        }
-        ws = slot.first;
-        wsb = slot.second;
-    }
+    rc = stream_workspace(dev, stream, pl.total_ws, &ws, &wsb);
+    if (rc) return rc;
     return run_decode(c, llr, n_frames, L, algo, pr, quant, info_out, status_out, pm_out, ws, wsb,
                       (cudaStream_t)stream, pl);
+}
+
+// ---------------------------------------------------------------------------
+// Decode from host buffers (pscl_decode_host): the batch is cut into up to
+// kHostChunks chunks; one internal stream copies the chunks' LLRs in, two
+// decode them alternately (each with its own workspace) and copy their
+// outputs back, so copies and decodes of different chunks overlap, and a
+// chunk's decode may start while the previous one drains.  Per (device,
+// caller stream): the streams, events and a device staging buffer.
+constexpr int kHostChunks = 4;
+constexpr int kHostMinChunk = 4096;  // frames: smaller batches are not cut
+struct HostCtx {
+    cudaStream_t copy = nullptr;
+    cudaStream_t comp[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_done[2] = {nullptr, nullptr}, ev_in[kHostChunks] = {};
+    void *dbuf = nullptr;
+    size_t dbytes = 0;
+};
+static std::map<std::pair<int, void *>, HostCtx> g_host;
+
+static int host_ctx(int dev, void *stream, size_t bytes, HostCtx **out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    HostCtx &h = g_host[std::make_pair(dev, stream)];
+    if (!h.copy) {
+        CU(cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&h.comp[0], cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&h.comp[1], cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&h.ev_start, cudaEventDisableTiming));
+        for (auto &e : h.ev_done) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto &e : h.ev_in) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (h.dbytes < bytes) {
+        if (h.dbuf) {
+            // earlier calls' copies and decodes may still use it
+            CU(cudaStreamSynchronize(h.copy));
+            CU(cudaStreamSynchronize(h.comp[0]));
+            CU(cudaStreamSynchronize(h.comp[1]));
+            lib_free(h.dbuf);
+            h.dbuf = nullptr;
+            h.dbytes = 0;
+        }
+        const size_t want = bytes + bytes / 4;
+        CU(cudaMalloc(&h.dbuf, want));
+        h.dbytes = want;
+    }
+    *out = &h;
+    return PSCL_OK;
+}
+
+extern "C" int pscl_decode_host(pscl_code c, const float *llr_host, int n_frames, int L, pscl_algo algo,
+                                const pscl_pruning *pr, pscl_quant quant, uint8_t *info_host,
+                                int32_t *status_host, void *stream)
+{
+    // every argument error is reported before anything is enqueued
+    Plan pl;
+    int rc = make_plan(c, n_frames, L, algo, pr, quant, &pl);
+    if (rc) return rc;
+    if (n_frames == 0) return PSCL_OK;
+    if (!llr_host || !info_host || !status_host)
+        return fail(PSCL_EINVAL, "llr_host, info_host and status_host are required");
+    int dev;
+    CU(cudaGetDevice(&dev));
+    const size_t row = (size_t)(c->N - c->P), nb = (size_t)((c->kinfo + 7) / 8);
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t off_info = up((size_t)n_frames * row * 4), off_status = off_info + up((size_t)n_frames * nb);
+    HostCtx *h = nullptr;
+    rc = host_ctx(dev, stream, off_status + (size_t)n_frames * 4, &h);
+    if (rc) return rc;
+    float *llr_d = (float *)h->dbuf;
+    uint8_t *info_d = (uint8_t *)h->dbuf + off_info;
+    int32_t *status_d = (int32_t *)((char *)h->dbuf + off_status);
+    int k = n_frames / kHostMinChunk;
+    k = k < 1 ? 1 : (k > kHostChunks ? kHostChunks : k);
+    const int per = (n_frames + k - 1) / k;
+    CU(cudaEventRecord(h->ev_start, (cudaStream_t)stream));
+    CU(cudaStreamWaitEvent(h->copy, h->ev_start, 0));
+    CU(cudaStreamWaitEvent(h->comp[0], h->ev_start, 0));
+    CU(cudaStreamWaitEvent(h->comp[1], h->ev_start, 0));
+    for (int i = 0; i < k; i++) {
+        const size_t f0 = (size_t)i * per, m = std::min((size_t)per, (size_t)n_frames - f0);
+        CU(cudaMemcpyAsync(llr_d + f0 * row, llr_host + f0 * row, m * row * 4, cudaMemcpyHostToDevice, h->copy));
+        CU(cudaEventRecord(h->ev_in[i], h->copy));
+    }
+    for (int i = 0; i < k; i++) {
+        const size_t f0 = (size_t)i * per, m = std::min((size_t)per, (size_t)n_frames - f0);
+        cudaStream_t s = h->comp[i & 1];
+        CU(cudaStreamWaitEvent(s, h->ev_in[i], 0));
+        rc = pscl_decode(c, llr_d + f0 * row, (int)m, L, algo, pr, quant, info_d + f0 * nb, status_d + f0, nullptr,
+                         (void *)s);
+        if (rc) return rc;
+        CU(cudaMemcpyAsync(info_host + f0 * nb, info_d + f0 * nb, m * nb, cudaMemcpyDeviceToHost, s));
+        CU(cudaMemcpyAsync(status_host + f0, status_d + f0, m * 4, cudaMemcpyDeviceToHost, s));
+    }
+    for (int j = 0; j < 2; j++) {
+        CU(cudaEventRecord(h->ev_done[j], h->comp[j]));
+        CU(cudaStreamWaitEvent((cudaStream_t)stream, h->ev_done[j], 0));
+    }
+    return PSCL_OK;
 }
 
 extern "C" int pscl_decode_ws(pscl_code c, const float *llr, int n_frames, int L, pscl_algo algo,

@@ -89,6 +89,7 @@ def lib() -> C.CDLL:
             L.pscl_decode_ws.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp, C.c_size_t, vp]
             L.pscl_encode.argtypes = [vp, vp, i, vp, vp]
             L.pscl_decode_static.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp, vp]
+            L.pscl_decode_host.argtypes = [vp, vp, i, i, i, vp, i, vp, vp, vp]
             L.pscl_code_tune.argtypes = [vp, i, i, vp, i, i, i, i]
             L.pscl_server_start.argtypes = [vp, C.POINTER(vp)]
             L.pscl_server_submit.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
@@ -188,6 +189,15 @@ def pscl_decode(code, llr, n_frames, L, algo, prune, quant, info_out, status_out
     return _check(lib().pscl_decode(code, _ptr(llr), n_frames, L, algo,
                                     C.byref(prune) if prune is not None else None, quant,
                                     _ptr(info_out), _ptr(status_out), _ptr(pm_out), _stream(stream)))
+
+
+def pscl_decode_host(code, llr_host, n_frames, L, algo, prune, quant, info_host, status_host, stream=None):
+    """llr_host, info_host, status_host: CPU tensors or numpy arrays (page-locked
+    tensors let the copies overlap the decodes); synchronize `stream` before
+    reading the outputs."""
+    return _check(lib().pscl_decode_host(code, _ptr(llr_host), n_frames, L, algo,
+                                         C.byref(prune) if prune is not None else None, quant,
+                                         _ptr(info_host), _ptr(status_host), _stream(stream)))
 
 
 def pscl_workspace_size(code, n_frames, L, algo, prune, quant) -> int:
