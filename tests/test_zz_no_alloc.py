@@ -63,3 +63,26 @@ def test_static_scratch_rejects_oversized_and_unprepared_calls():
     with pytest.raises(ps.PsclError) as e:
         ps.pscl_decode_static(g.handle, t, 8, 4, 1, ps.pruning(15, rep_max=2), 0, info, status)
     assert "pscl_prepare" in str(e.value)
+
+
+def test_static_calls_leave_device_memory_unchanged():
+    """After set-up, further static calls take no device memory: the free
+    memory the driver reports is the same before and after them (the GPU
+    is this process's alone while the tests run)."""
+    import torch
+    from paper_1710_08314_gb300 import polarscl as ps
+    d = synth.load_code("c2_2048_1723")
+    g = gpu_code(d)
+    ps.pscl_prepare(g.handle, None)
+    _, _, llr = make_inputs(d, 256, 3.0, 41)
+    t = torch.from_numpy(llr).cuda()
+    info = torch.empty((256, g.nbytes), dtype=torch.uint8, device="cuda")
+    status = torch.empty((256,), dtype=torch.int32, device="cuda")
+    ps.pscl_decode_static(g.handle, t, 256, 32, ps.PSCL_CASCL, None, ps.PSCL_F32, info, status)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        ps.pscl_decode_static(g.handle, t, 256, 32, ps.PSCL_CASCL, None, ps.PSCL_F32, info, status)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
