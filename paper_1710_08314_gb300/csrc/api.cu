@@ -439,7 +439,7 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, b
 // 16..31 (an h step the offset of the node it completes).
 // Unpruned subtrees of up to kScFuse leaves are one step (OP_RSUB, decoded
 // in registers; the kernel reads their frozen leaves from the code's mask).
-constexpr int kScFuse = 8;
+constexpr int kScFuse = 16;
 
 static void gen_sc_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int o, int S, int side,
                            std::vector<uint32_t> &ops, int &max_depth)

@@ -20,7 +20,7 @@
 //     tree over index order (per-lane chunks, then a butterfly across lanes),
 //     the same tree the list decoder and the oracle use.
 // The schedule is the pruned tree of the list decoder, each step carrying its
-// node's leaf offset (bits 16..31); unpruned subtrees of up to 8 leaves are
+// node's leaf offset (bits 16..31); unpruned subtrees of up to 16 leaves are
 // one step, decoded in registers by every lane alike, and so are the node
 // handlers of nodes up to 8 positions.  The warp reads its schedule 32 steps
 // at a time (a lane per step) and passes the steps round by shuffles.
@@ -268,7 +268,7 @@ struct ScFrame {
         }
     }
 
-    // an unpruned subtree of S leaves (S = 2, 4, 8) decoded in registers by
+    // an unpruned subtree of S leaves (S = 2, 4, 8, 16) decoded in registers by
     // every lane alike: f, g and h of Sec. II-B, information leaves take the
     // hard decision, frozen leaves add their penalty; returns its S bits
     template <int S>
@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(128, ScBlocks<Qt>::value) sc_kernel(const __gr
                 switch (N >> d) {
                 case 2: f.template rsub_step<2>(d, o, pm); break;
                 case 4: f.template rsub_step<4>(d, o, pm); break;
-                default: f.template rsub_step<8>(d, o, pm); break;  // the host emits 2, 4 or 8
+                case 8: f.template rsub_step<8>(d, o, pm); break;
+                default: f.template rsub_step<16>(d, o, pm); break;  // the host emits 2, 4, 8 or 16
                 }
                 break;
             default: f.node(d, o, (int)op_type(op), pm); break;
