@@ -437,8 +437,10 @@ static int gen_program(const pscl_code_s *c, const pscl_pruning *pr, int fuse, b
 // The schedule of the one-path (SC) kernel: the same pruned tree without
 // register subtrees; every step carries its node's leaf offset in bits
 // 16..31 (an h step the offset of the node it completes).
-// Unpruned subtrees of up to kScFuse leaves are one step (OP_RSUB, decoded
-// in registers; the kernel reads their frozen leaves from the code's mask).
+// Subtrees of up to kScFuse leaves are one step (OP_RSUB, decoded in
+// registers; the kernel reads their frozen leaves from the code's mask and,
+// when the step's t field is 1, the pruned nodes inside them from the
+// node-type words stored after the schedule, see sc_node_types).
 constexpr int kScFuse = 16;
 
 static void gen_sc_program(const pscl_code_s *c, const pscl_pruning *pr, int d, int o, int S, int side,
@@ -451,8 +453,9 @@ static void gen_sc_program(const pscl_code_s *c, const pscl_pruning *pr, int d, 
         if (d > max_depth) max_depth = d;
         return;
     }
-    if (d >= 1 && S <= kScFuse && subtree_unpruned(c, pr, o, S)) {
-        ops.push_back(op_make(OP_RSUB, (uint32_t)d, 0, (uint32_t)side, 0) | off);
+    if (d >= 1 && S <= kScFuse) {
+        const uint32_t t = subtree_unpruned(c, pr, o, S) ? 0u : 1u;  // 1: pruned nodes inside
+        ops.push_back(op_make(OP_RSUB, (uint32_t)d, 0, (uint32_t)side, t) | off);
         if (d > max_depth) max_depth = d;
         return;
     }
@@ -461,6 +464,30 @@ static void gen_sc_program(const pscl_code_s *c, const pscl_pruning *pr, int d, 
     ops.push_back(op_make(OP_G, (uint32_t)d, 0, 0, 0) | off);
     gen_sc_program(c, pr, d + 1, o + S / 2, S / 2, 1, ops, max_depth);
     if (d > 0) ops.push_back(op_make(OP_COMB, (uint32_t)(d + 1), 0, (uint32_t)side, 0) | off);
+}
+
+// Node types inside the SC kernel's register subtrees: for each group of 16
+// leaves (g = 0 .. ceil(N/16) - 1) one 64-bit word holding, for the group's
+// nodes of 2..16 leaves in heap order (node h = 1 .. 15: size 16 >> floor(log2
+// h), offset g*16 + (h - 2^floor(log2 h)) * size), the pruned-node type at
+// bits 3(h-1) (0: not a pruned node); appended to the schedule as pairs of
+// 32-bit words from an even index.
+static void sc_node_types(const pscl_code_s *c, const pscl_pruning *pr, std::vector<uint32_t> &ops)
+{
+    if (ops.size() & 1) ops.push_back(0u);
+    const int groups = (c->N + 15) / 16;
+    for (int g = 0; g < groups; g++) {
+        uint64_t w = 0;
+        for (int h = 1; h < 16; h++) {
+            int l = 0;
+            while ((2 << l) <= h) l++;
+            const int S = 16 >> l, o = g * 16 + (h - (1 << l)) * S;
+            if (o + S > c->N) continue;
+            w |= (uint64_t)classify(c, pr, o, S) << (3 * (h - 1));
+        }
+        ops.push_back((uint32_t)w);
+        ops.push_back((uint32_t)(w >> 32));
+    }
 }
 
 // Peephole fusion of the schedule: a right register-subtree pair (or quad)
@@ -540,6 +567,7 @@ static int get_program(pscl_code c, const pscl_pruning *pr, int fuse, bool fixed
     p.root_special = (op_code(ops[0]) == OP_NODE) ? 1 : 0;
     for (uint32_t w : ops)
         if (op_code(w) == OP_NODE) p.has_nodes = 1;
+    if (fuse == 0) sc_node_types(c, eff, ops);  // after the n_ops schedule steps
     CU(cudaMalloc(&p.d_ops, ops.size() * sizeof(uint32_t)));
     cudaError_t e = cudaMemcpy(p.d_ops, ops.data(), ops.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

@@ -20,9 +20,9 @@
 //     tree over index order (per-lane chunks, then a butterfly across lanes),
 //     the same tree the list decoder and the oracle use.
 // The schedule is the pruned tree of the list decoder, each step carrying its
-// node's leaf offset (bits 16..31); unpruned subtrees of up to 16 leaves are
-// one step, decoded in registers by every lane alike, and so are the node
-// handlers of nodes up to 8 positions.  The warp reads its schedule 32 steps
+// node's leaf offset (bits 16..31); subtrees of up to 16 leaves are one step,
+// decoded in registers by every lane alike together with the pruned nodes
+// inside them, and so are the node handlers of nodes up to 8 positions.  The warp reads its schedule 32 steps
 // at a time (a lane per step) and passes the steps round by shuffles.
 #include <map>
 #include <mutex>
@@ -215,19 +215,17 @@ struct ScFrame {
         }
     }
 
-    // a node of S <= 8 positions: every lane reads all of them and takes the
-    // same decision, so no lane has to wait for another
+    // a node of S <= 16 positions whose values every lane holds: every lane
+    // takes the same decision, so no lane has to wait for another; returns
+    // the node's partial-sum bits
     template <int S>
-    __device__ void node_small(int d, int o, int type, V &pm)
+    __device__ uint32_t node_regs(const V (&a)[S], int type, V &pm) const
     {
-        V a[S];
-        load_small<S>(d, a);
         uint32_t h = 0;
 #pragma unroll
         for (int i = 0; i < S; ++i) h |= (uint32_t)(a[i] < 0) << i;
-        if (type == NT_R1) {
-            put_small(o, S, h);
-        } else if (type == NT_R0) {
+        if (type == NT_R1) return h;
+        if (type == NT_R0) {
             if (!Qt::FIXED) {
                 TreeSum<Qt> t0;
                 V p0 = Qt::zero();
@@ -235,8 +233,9 @@ struct ScFrame {
                 for (int i = 0; i < S; ++i) p0 = t0.push(a[i] < 0 ? Qt::absv(a[i]) : Qt::zero(), i);
                 pm = Qt::add(pm, p0);
             }
-            put_small(o, S, 0u);
-        } else if (type == NT_REP) {
+            return 0u;
+        }
+        if (type == NT_REP) {
             TreeSum<Qt> t0, t1;
             V p0 = Qt::zero(), p1 = Qt::zero();
 #pragma unroll
@@ -247,32 +246,43 @@ struct ScFrame {
             const V c0 = Qt::add(Qt::FIXED ? Qt::zero() : pm, p0), c1 = Qt::add(Qt::FIXED ? Qt::zero() : pm, p1);
             const bool ones = Qt::key(c1) < Qt::key(c0);
             if (!Qt::FIXED) pm = ones ? c1 : c0;
-            put_small(o, S, ones ? 0xFFFFFFFFu : 0u);
-        } else {
-            // SPC: odd parity flips the least reliable position (smallest (|a|, i))
-            if (__popc(h) & 1) {
-                int r0 = 0;
-                uint32_t kb = Qt::key(Qt::absv(a[0]));
-#pragma unroll
-                for (int i = 1; i < S; ++i) {
-                    const uint32_t k = Qt::key(Qt::absv(a[i]));
-                    if (k < kb) {
-                        kb = k;
-                        r0 = i;
-                    }
-                }
-                h ^= 1u << r0;
-                if (!Qt::FIXED) pm = Qt::add(pm, Qt::add(Qt::zero(), Qt::from_key(kb)));
-            }
-            put_small(o, S, h);
+            return ones ? 0xFFFFFFFFu : 0u;
         }
+        // SPC: odd parity flips the least reliable position (smallest (|a|, i))
+        if (__popc(h) & 1) {
+            int r0 = 0;
+            uint32_t kb = Qt::key(Qt::absv(a[0]));
+#pragma unroll
+            for (int i = 1; i < S; ++i) {
+                const uint32_t k = Qt::key(Qt::absv(a[i]));
+                if (k < kb) {
+                    kb = k;
+                    r0 = i;
+                }
+            }
+            h ^= 1u << r0;
+            if (!Qt::FIXED) pm = Qt::add(pm, Qt::add(Qt::zero(), Qt::from_key(kb)));
+        }
+        return h;
     }
 
-    // an unpruned subtree of S leaves (S = 2, 4, 8, 16) decoded in registers by
-    // every lane alike: f, g and h of Sec. II-B, information leaves take the
-    // hard decision, frozen leaves add their penalty; returns its S bits
+    // a node of S <= 8 positions: every lane reads all of them
     template <int S>
-    __device__ uint32_t rsub(const V (&a)[S], uint32_t fz, V &pm) const
+    __device__ void node_small(int d, int o, int type, V &pm)
+    {
+        V a[S];
+        load_small<S>(d, a);
+        put_small(o, S, node_regs<S>(a, type, pm));
+    }
+
+    // a subtree of S leaves (S = 2, 4, 8, 16) decoded in registers by every
+    // lane alike: f, g and h of Sec. II-B, information leaves take the hard
+    // decision, frozen leaves add their penalty; with NODES, a pruned node
+    // inside it (its type in desc: 3 bits per node of the enclosing 16-leaf
+    // group, node h of the group in heap order at bits 3(h-1)) is decided as
+    // one.  Returns its S bits.
+    template <int S, bool NODES>
+    __device__ uint32_t rsub(const V (&a)[S], uint32_t fz, V &pm, uint64_t desc, int h) const
     {
         if constexpr (S == 1) {
             if (fz & 1u) {
@@ -281,26 +291,37 @@ struct ScFrame {
             }
             return (uint32_t)(a[0] < 0);
         } else {
+            if constexpr (NODES) {
+                const int type = (int)((desc >> (3 * (h - 1))) & 7u);
+                if (type != 0) return node_regs<S>(a, type, pm);
+            }
             constexpr int H = S / 2;
             V l[H], r[H];
 #pragma unroll
             for (int i = 0; i < H; ++i) l[i] = Qt::f1(a[i], a[i + H]);
-            const uint32_t bl = rsub<H>(l, fz, pm);
+            const uint32_t bl = rsub<H, NODES>(l, fz, pm, desc, 2 * h);
 #pragma unroll
             for (int i = 0; i < H; ++i) r[i] = Qt::g1(a[i], a[i + H], (bl >> i) & 1u);
-            const uint32_t br = rsub<H>(r, fz >> H, pm);
+            const uint32_t br = rsub<H, NODES>(r, fz >> H, pm, desc, 2 * h + 1);
             constexpr uint32_t m = (1u << H) - 1u;
             return ((bl ^ br) & m) | ((br & m) << H);
         }
     }
 
+    // nodes: the host found pruned nodes inside the subtree (step field t)
     template <int S>
-    __device__ void rsub_step(int d, int o, V &pm)
+    __device__ void rsub_step(int d, int o, bool nodes, V &pm)
     {
         V a[S];
         load_small<S>(d, a);
         const uint32_t fz = ~(__ldg(&P.code.amask[o >> 5]) >> (o & 31));
-        put_small(o, S, rsub<S>(a, fz, pm));
+        if (nodes) {
+            // node types of the 16-leaf groups, after the schedule (8-byte aligned)
+            const uint64_t *desc = reinterpret_cast<const uint64_t *>(P.ops + ((P.n_ops + 1) & ~1));
+            put_small(o, S, rsub<S, true>(a, fz, pm, __ldg(&desc[o >> 4]), 16 / S + (o & 15) / S));
+        } else {
+            put_small(o, S, rsub<S, false>(a, fz, pm, 0, 1));
+        }
     }
 
     // a leaf or pruned node at depth d, leaf offset o
@@ -460,10 +481,10 @@ __global__ void __launch_bounds__(128, ScBlocks<Qt>::value) sc_kernel(const __gr
             case OP_COMB: f.comb(N >> d, o); break;
             case OP_RSUB:
                 switch (N >> d) {
-                case 2: f.template rsub_step<2>(d, o, pm); break;
-                case 4: f.template rsub_step<4>(d, o, pm); break;
-                case 8: f.template rsub_step<8>(d, o, pm); break;
-                default: f.template rsub_step<16>(d, o, pm); break;  // the host emits 2, 4, 8 or 16
+                case 2: f.template rsub_step<2>(d, o, op_t(op) != 0, pm); break;
+                case 4: f.template rsub_step<4>(d, o, op_t(op) != 0, pm); break;
+                case 8: f.template rsub_step<8>(d, o, op_t(op) != 0, pm); break;
+                default: f.template rsub_step<16>(d, o, op_t(op) != 0, pm); break;  // the host emits 2, 4, 8 or 16
                 }
                 break;
             default: f.node(d, o, (int)op_type(op), pm); break;

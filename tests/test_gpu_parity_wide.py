@@ -183,13 +183,17 @@ def test_custom_crcs_and_density_evolution_codes(pool, name):
 
 @pytest.mark.parametrize("name", ["c1_cascl_128_64_L4", "u09", "u43", "c2_2048_1723", "ln_8192_4096", "crc6_512_256"])
 @pytest.mark.parametrize("quant", ["f32", "i16", "i8"])
-@pytest.mark.parametrize("prune", [None, "all"])
+@pytest.mark.parametrize("prune", [None, "all", "spc_any"])
 def test_sc_kernel_equals_the_oracle_and_the_list_kernel(pool, name, quant, prune):
     """One-path decoding (SC) on the warp-per-frame kernel and on the list
-    kernel: identical bits, status and metric, equal to the oracle."""
+    kernel: identical bits, status and metric, equal to the oracle.  The SC
+    kernel decides pruned nodes of up to 16 leaves inside its register
+    subtrees; SPC nodes of any size ("spc_any") put SPC nodes of 8 and 16
+    leaves there too."""
     from paper_1710_08314_gb300 import polarscl as ps, pruning
     d = synth.load_code(name)
-    p = None if prune is None else dict(mask=15, rep_max=8 if quant == "i8" else 0, spc_max=4, r1_t=2, spc_t=4)
+    p = None if prune is None else dict(mask=15, rep_max=8 if quant == "i8" else 0,
+                                        spc_max=0 if prune == "spc_any" else 4, r1_t=2, spc_t=4)
     gp = pruning(**p) if p else None
     n = 300 if d["N"] <= 2048 else 64
     code, _, llr = make_inputs(d, n, 1.0 if d["N"] < 2048 else 3.0, 990)
