@@ -1006,7 +1006,7 @@ def main():
         line["cpu_baseline"] = {"value": cpu[0], "unit": "Mb/s", "cores": cpu[1], "kind": "oracle",
                                 "sample": cpu[2], "single_thread": cpu[3]}
     if not args.headline_only:
-        del llr, llr_h, llr_d
+        del llr, llr_h
         torch.cuda.empty_cache()
         g2 = torch.Generator(device="cuda")
         g2.manual_seed(77)

@@ -357,8 +357,9 @@ int pscl_server_stop(pscl_server s, int timeout_ms);
 int pscl_set_tuning(int target_warps_per_sm);
 int pscl_set_fusion(int max_leaves);
 /* pscl_set_sc_kernel: 1 (default) decodes one-path stages (PSCL_SC, and the
- * first stage of PSCL_FASCL and PSCL_PASCL) of batches up to four waves of
- * resident warps with a warp per frame and all of a frame's LLR layers and
+ * first stage of PSCL_FASCL and PSCL_PASCL) of batches up to six waves of
+ * resident warps in float (two and a half in fixed point; about 22 k and
+ * 12 k frames at N = 2048) with a warp per frame and all of a frame's LLR layers and
  * partial sums in shared memory (lowest latency); larger batches, and every
  * batch with 0, go to the list kernel, which decodes 32 such frames per warp
  * (highest throughput).  Results are identical; not thread-safe against

@@ -733,9 +733,11 @@ static void make_sc_layout(const pscl_code_s *c, const Program &pg, int quant, L
 }
 
 // one-path stages (SC, the first stage of FA and PA) of batches of up to
-// kScWaves waves of resident warps use the SC kernel
+// kScQuarterWaves[float, fixed] / 4 waves of resident warps use the SC
+// kernel (measured crossovers with the list kernel on (2048,1723) at 4.5 dB:
+// about 6 waves in float, between 2 and 3 in fixed point)
 static bool g_sc_kernel = true;
-constexpr long long kScWaves = 4;
+constexpr long long kScQuarterWaves[2] = {24, 10};
 
 // ---------------------------------------------------------------------------
 // launch plan for one decode call
@@ -854,10 +856,10 @@ static int make_plan(pscl_code c, int n_frames, int L, pscl_algo algo, const psc
         // A warp spends far more instructions per frame than a lane of the
         // list kernel, which decodes 32 one-path frames per warp side by side,
         // but it finishes its frame about five times sooner: the SC kernel
-        // takes batches of up to kScWaves waves of resident warps, where it
+        // takes batches of up to a few waves of resident warps, where it
         // finishes first; larger batches go to the list kernel.
         const long long smax = (long long)dp.sms * sbps * kWarpsPerBlock;
-        if (sbps >= 1 && (long long)n_frames <= kScWaves * smax) {
+        if (sbps >= 1 && 4 * (long long)n_frames <= kScQuarterWaves[fixed ? 1 : 0] * smax) {
             const long long sw = n_frames < 1 ? 1 : (n_frames < smax ? n_frames : smax);
             pl->sc_grid = (int)((sw + kWarpsPerBlock - 1) / kWarpsPerBlock);
             pl->sc_total_warps = pl->sc_grid * kWarpsPerBlock;
