@@ -54,3 +54,39 @@ def test_snr_at_fer_interpolates_in_log_domain():
 
 def test_both_arms_report_the_same_config():
     assert bench.headline_config("f32", bench.BATCH, 1) == bench.headline_config()
+
+
+def test_bench_source_refers_only_to_names_it_defines():
+    """The benchmark's GPU-only code paths cannot run here, so check by
+    reading: every global a function reads exists at module level (or is a
+    builtin), and every name a function deletes is assigned in it."""
+    import ast
+    import builtins
+    import os
+    import symtable
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py")
+    src = open(path).read()
+    top = symtable.symtable(src, path, "exec")
+    module_names = set(top.get_identifiers())
+    bad = []
+
+    def walk(t):
+        for ch in t.get_children():
+            if ch.get_type() == "function":
+                for s in ch.get_symbols():
+                    n = s.get_name()
+                    if s.is_global() and s.is_referenced() and n not in module_names and not hasattr(builtins, n):
+                        bad.append((ch.get_name(), n))
+            walk(ch)
+
+    walk(top)
+    for f in ast.walk(ast.parse(src)):
+        if isinstance(f, (ast.FunctionDef, ast.AsyncFunctionDef)):
+            assigned = {n.id for n in ast.walk(f) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Store)}
+            assigned |= {a.arg for a in f.args.args + f.args.kwonlyargs}
+            for d in (n for n in ast.walk(f) if isinstance(n, ast.Delete)):
+                for tg in d.targets:
+                    for nm in ast.walk(tg):
+                        if isinstance(nm, ast.Name) and nm.id not in assigned:
+                            bad.append((f.name, nm.id))
+    assert not bad, bad
