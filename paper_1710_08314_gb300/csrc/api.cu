@@ -459,6 +459,15 @@ static void gen_sc_program(const pscl_code_s *c, const pscl_pruning *pr, int d, 
         if (d > max_depth) max_depth = d;
         return;
     }
+    if (d >= 1 && S == 2 * kScFuse) {
+        // f, both register subtrees, g and h as one step; t bits: pruned
+        // nodes inside the left / right half
+        const uint32_t t = (subtree_unpruned(c, pr, o, S / 2) ? 0u : 1u) |
+                           (subtree_unpruned(c, pr, o + S / 2, S / 2) ? 0u : 2u);
+        ops.push_back(op_make(OP_RSUB2, (uint32_t)d, 0, (uint32_t)side, t) | off);
+        if (d > max_depth) max_depth = d;
+        return;
+    }
     ops.push_back(op_make(OP_F, (uint32_t)d, 0, 0, 0) | off);
     gen_sc_program(c, pr, d + 1, o, S / 2, 0, ops, max_depth);
     ops.push_back(op_make(OP_G, (uint32_t)d, 0, 0, 0) | off);

@@ -324,6 +324,33 @@ struct ScFrame {
         }
     }
 
+    // a 32-leaf subtree as one step: f into registers, the left 16-leaf
+    // subtree, g from the node's values read again, the right one, and the
+    // node's h; t bit 0 / bit 1: pruned nodes inside the left / right half
+    __device__ void rsub2_step(int d, int o, int t, V &pm)
+    {
+        constexpr int H = 16;
+        const uint32_t fz = ~(__ldg(&P.code.amask[o >> 5]) >> (o & 31));
+        const uint64_t *desc = reinterpret_cast<const uint64_t *>(P.ops + ((P.n_ops + 1) & ~1));
+        uint32_t bl, br;
+        {
+            V a[2 * H], l[H];
+            load_small<2 * H>(d, a);
+#pragma unroll
+            for (int i = 0; i < H; ++i) l[i] = Qt::f1(a[i], a[i + H]);
+            bl = (t & 1) ? rsub<H, true>(l, fz, pm, __ldg(&desc[o >> 4]), 1) : rsub<H, false>(l, fz, pm, 0, 1);
+        }
+        {
+            V a[2 * H], r[H];
+            load_small<2 * H>(d, a);
+#pragma unroll
+            for (int i = 0; i < H; ++i) r[i] = Qt::g1(a[i], a[i + H], (bl >> i) & 1u);
+            br = (t & 2) ? rsub<H, true>(r, fz >> H, pm, __ldg(&desc[(o >> 4) + 1]), 1)
+                         : rsub<H, false>(r, fz >> H, pm, 0, 1);
+        }
+        put_small(o, 2 * H, ((bl ^ br) & 0xFFFFu) | (br << H));
+    }
+
     // a leaf or pruned node at depth d, leaf offset o
     __device__ void node(int d, int o, int type, V &pm)
     {
@@ -487,6 +514,7 @@ __global__ void __launch_bounds__(128, ScBlocks<Qt>::value) sc_kernel(const __gr
                 default: f.template rsub_step<16>(d, o, op_t(op) != 0, pm); break;  // the host emits 2, 4, 8 or 16
                 }
                 break;
+            case OP_RSUB2: f.rsub2_step(d, o, op_t(op), pm); break;  // 32 leaves
             default: f.node(d, o, (int)op_type(op), pm); break;
             }
             __syncwarp();
