@@ -41,7 +41,7 @@ ALGO_NAMES = {"cascl": "CA-SCL", "sc": "SC", "fascl": "FA-SSCL"}
 
 def headline_config(quant: str = "f32", batch: int = BATCH, ws: int = 1, algo: str = "cascl",
                     pruned: bool = False, node_min: int = 0) -> dict:
-    """The workload both arms report (the driver compares the two lines);
+    """The workload both arms report (so that their lines compare);
     --algo / --pruned select another decode of the same frames (profiling)."""
     pn = ("pruned" + (f" (nodes of {node_min}+ leaves)" if node_min > 2 else "")) if pruned else "unpruned"
     return {"workload": f"{ALGO_NAMES[algo]} (2048,1723 incl. CRC-32) L=32 {quant} "

@@ -67,7 +67,7 @@ def test_static_scratch_rejects_oversized_and_unprepared_calls():
 
 def test_static_calls_leave_device_memory_unchanged():
     """After set-up, further static calls take no device memory: the free
-    memory the driver reports is the same before and after them (the GPU
+    memory that cudaMemGetInfo reports is the same before and after them (the GPU
     is this process's alone while the tests run)."""
     import torch
     from paper_1710_08314_gb300 import polarscl as ps
