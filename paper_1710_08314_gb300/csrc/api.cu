@@ -343,11 +343,17 @@ static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
 }
 
 // defaults of the two tuning knobs: the largest subtree decoded in registers
-// (2, 4 or 8 leaves; 1 = none) and the resident warps per SM the per-warp
-// shared-memory slice is sized for; per code and (L, format) the autotuner's
-// measurements override them (pscl_code_tune)
-static int g_fuse_max = 8;
+// (2, 4 or 8 leaves; 1 = none; 0 = by format: 4 leaves in float, 2 in fixed
+// point, the sizes the autotuner settles at for most codes) and the resident
+// warps per SM the per-warp shared-memory slice is sized for; per code and
+// (L, format) the autotuner's measurements override them (pscl_code_tune)
+static int g_fuse_max = 0;
 static int g_target_warps_per_sm = 28;
+
+static int default_fuse(int quant)
+{
+    return g_fuse_max ? g_fuse_max : (quant == PSCL_F32 ? 4 : 2);
+}
 
 static int tune_key(int L, int quant, const pscl_pruning *pr)
 {
@@ -360,7 +366,7 @@ static void tuning_for(pscl_code c, int L, int quant, const pscl_pruning *pr, in
                        int *res = nullptr)
 {
     *wps = g_target_warps_per_sm;
-    *fuse = g_fuse_max;
+    *fuse = default_fuse(quant);
     if (wpb) *wpb = kWarpsPerBlock;
     if (res) *res = g_target_warps_per_sm;
     std::lock_guard<std::mutex> lk(c->mu);
@@ -606,7 +612,8 @@ extern "C" int pscl_prepare(pscl_code c, const pscl_pruning *pr)
 {
     if (!c) return fail(PSCL_EINVAL, "code is NULL");
     // the default schedule and every fusion size the code's tuning uses
-    std::vector<int> fuses = {g_fuse_max, 0};  // 0: the one-path (SC) kernel's schedule
+    // 0: the one-path (SC) kernel's schedule
+    std::vector<int> fuses = {default_fuse(PSCL_F32), default_fuse(PSCL_I16), 0};
     {
         std::lock_guard<std::mutex> lk(c->mu);
         for (auto &kv : c->tune) fuses.push_back(kv.second.fuse);
@@ -1201,8 +1208,8 @@ extern "C" int pscl_set_sc_kernel(int enable)
 
 extern "C" int pscl_set_fusion(int max_leaves)
 {
-    if (max_leaves != 1 && max_leaves != 2 && max_leaves != 4 && max_leaves != 8)
-        return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8", max_leaves);
+    if (max_leaves != 0 && max_leaves != 1 && max_leaves != 2 && max_leaves != 4 && max_leaves != 8)
+        return fail(PSCL_EINVAL, "fusion size %d: must be 1, 2, 4 or 8 (0 = by format)", max_leaves);
     g_fuse_max = max_leaves;
     return PSCL_OK;
 }

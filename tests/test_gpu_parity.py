@@ -171,7 +171,7 @@ def test_every_fusion_depth_gives_identical_results(fuse):
         run_case("u09", 200, 1.0, 8, "cascl", "i16", None, 60 + fuse)
         run_case("c2_2048_1723", 64, 3.5, 16, "cascl", "f32", None, 70 + fuse, frames=np.array([0, 63]))
     finally:
-        ps.pscl_set_fusion(8)
+        ps.pscl_set_fusion(0)
 
 
 @pytest.mark.parametrize("wps", [4, 16, 28])

@@ -158,7 +158,7 @@ def test_depth_beyond_the_slot_tables_is_refused():
             g.decode(torch.zeros((4, 8192), device="cuda"), 8)
         assert e.value.code == ps.PSCL_EUNSUPPORTED
     finally:
-        ps.pscl_set_fusion(8)
+        ps.pscl_set_fusion(0)
 
 
 @pytest.mark.parametrize("name", ["crc6_512_256", "crc11_512_256", "crc24_512_256", "de_1024_512"])
