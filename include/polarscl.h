@@ -131,7 +131,7 @@ int pscl_prepare(pscl_code code, const pscl_pruning *pruning);
  * the decoder's register cap: 24 or more selects the 72-register variant
  * (up to 28 warps per SM), less the 96-register (node-free, 20 warps) or
  * 128-register (node-capable, 16 warps) one.  (0, 0, 0, 0) restores the
- * defaults (28 warps, the pscl_set_fusion size, 4 warps per block).  Results never depend
+ * defaults (32 warps, the pscl_set_fusion size, 4 warps per block).  Results never depend
  * on the tuning.  Written by the package's autotuner.                      */
 int pscl_code_tune(pscl_code code, int L, pscl_quant quant, const pscl_pruning *pruning, int warps_per_sm,
                    int fuse_leaves, int warps_per_block, int resident_warps);
@@ -349,8 +349,9 @@ int pscl_server_stop(pscl_server s, int timeout_ms);
 /* Process-wide defaults, used where a code has no pscl_code_tune entry and
  * by every batch and server (no counterpart in the paper: GPU scheduling).
  * pscl_set_tuning: resident warps per SM the shared-memory slices are sized
- *   for, 1..64 (default 28); 24 and more select the 72-register decoder
- *   variant for schedules without pruned nodes.
+ *   for, 1..64 (default 32: 28 warps reside, the rest of the shared memory
+ *   serves as L1 cache); 24 and more select the 72-register decoder
+ *   variants.
  * pscl_set_fusion: largest register subtree, 1, 2, 4 or 8 leaves (1 =
  *   none; 0, the default, = by number format: 4 leaves in float, 2 in fixed
  *   point).  Not thread-safe against concurrent decodes; results never

@@ -348,7 +348,7 @@ static int classify(const pscl_code_s *c, const pscl_pruning *pr, int o, int S)
 // warps per SM the per-warp shared-memory slice is sized for; per code and
 // (L, format) the autotuner's measurements override them (pscl_code_tune)
 static int g_fuse_max = 0;
-static int g_target_warps_per_sm = 28;
+static int g_target_warps_per_sm = 32;  // with 28 resident: the rest of shared memory goes to L1
 
 static int default_fuse(int quant)
 {

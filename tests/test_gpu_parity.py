@@ -184,7 +184,7 @@ def test_shared_memory_budget_gives_identical_results(wps):
         run_case("c2_2048_1723", 256, 3.5, 32, "cascl", "f32", None, 80 + wps, frames=np.array([5, 255]))
         run_case("c3_1024_512_L8", 300, 2.0, 8, "cascl", "i8", "i8", 90 + wps, frames=np.arange(0, 300, 37))
     finally:
-        ps.pscl_set_tuning(28)  # the library's default target
+        ps.pscl_set_tuning(32)  # the library's default target
 
 
 @pytest.mark.parametrize("quant,scale", [("i8", 400.0), ("i8", 0.25), ("i16", 0.03125), ("f32", 1.0)])
