@@ -1134,7 +1134,18 @@ extern "C" int pscl_decode_host(pscl_code c, const float *llr_host, int n_frames
         CU(cudaStreamWaitEvent(s, h->ev_in[i], 0));
         rc = pscl_decode(c, llr_d + f0 * row, (int)m, L, algo, pr, quant, info_d + f0 * nb, status_d + f0, nullptr,
                          (void *)s);
-        if (rc) return rc;
+        if (rc) {
+            // a later chunk could not be enqueued (a device error): later
+            // work on `stream` still waits for what was, so the caller's
+            // buffers stay in use until it is done
+            for (int j = 0; j < 2; j++) {
+                cudaEventRecord(h->ev_done[j], h->comp[j]);
+                cudaStreamWaitEvent((cudaStream_t)stream, h->ev_done[j], 0);
+            }
+            cudaEventRecord(h->ev_in[0], h->copy);
+            cudaStreamWaitEvent((cudaStream_t)stream, h->ev_in[0], 0);
+            return rc;
+        }
         CU(cudaMemcpyAsync(info_host + f0 * nb, info_d + f0 * nb, m * nb, cudaMemcpyDeviceToHost, s));
         CU(cudaMemcpyAsync(status_host + f0, status_d + f0, m * 4, cudaMemcpyDeviceToHost, s));
     }
