@@ -90,3 +90,30 @@ def test_bench_source_refers_only_to_names_it_defines():
                         if isinstance(nm, ast.Name) and nm.id not in assigned:
                             bad.append((f.name, nm.id))
     assert not bad, bad
+
+
+@pytest.mark.parametrize("key", ["c2_2048_1723_L32_unpruned", "c3_1024_512_L8_L8_pruned_n64",
+                                 "c2_2048_1723_L1_pruned_n32", "c1_cascl_128_64_L4_L4_unpruned"])
+def test_stored_work_counts_are_the_oracles(key):
+    """The stored per-frame work counts the rooflines use are what the oracle
+    counts now (the generator, tests/golden/make_work_counts.py, is the
+    only writer)."""
+    import importlib.util
+    import json
+    import os
+    import numpy as np
+    import oracle
+    import synth
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("make_work_counts", os.path.join(here, "golden", "make_work_counts.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    stored = json.load(open(os.path.join(here, "golden", "work_per_frame.json")))[key]
+    name, L, pk = next((n, l, p) for n, l, p in gen.CASES if f"{n}_L{l}_{p or 'unpruned'}" == key)
+    d = synth.load_code(name)
+    code = oracle.Code(d["frozen"], d["crc_len"], d["crc_poly"], d["punct"], d["systematic"])
+    st = oracle.Stats()
+    oracle.decode(code, np.full(code.N - code.P, 3.0), L, oracle.CASCL,
+                  oracle.pruning(**gen.PRUNINGS[pk]) if pk else None, oracle.F32, stats=st)
+    assert (st.fg_elems, st.node_steps, st.sorts, st.cand_total) == (
+        stored["fg_elems"], stored["node_steps"], stored["sorts"], stored["cand_total"])
